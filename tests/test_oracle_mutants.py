@@ -1,0 +1,79 @@
+"""The pins are strong enough: plant plausible mistakes in a COPY of the oracle (a flipped
+comparison, a dropped element, an off-by-one, a transposed operand), compile each mutant on the
+CPU and check that at least one pin fails for it.  The oracle source itself is never changed."""
+import ctypes
+import math
+import subprocess
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_10913_gb300 import graphgen as gg
+
+SRC = Path(oracle.__file__).resolve().parent / "citron_oracle.c"
+
+# (name, original text, mutated text); every original must occur exactly once.
+MUTANTS = [
+    ("degree-direction", "return du < dv || (du == dv && u < v);", "return du > dv || (du == dv && u < v);"),
+    ("tie-break", "return du < dv || (du == dv && u < v);", "return du < dv || (du == dv && u > v);"),
+    ("prune-off-by-one", "if (len < (uint32_t)r) return ORACLE_OK;", "if (len <= (uint32_t)r) return ORACLE_OK;"),
+    ("leaf-size", "        *out = len;\n        return ORACLE_OK;", "        *out = len - (len > 1);\n        return ORACLE_OK;"),
+    ("merge-compare", "if (a[i] < b[j]) i++;", "if (a[i] <= b[j]) i++;"),
+    ("penultimate-drop-last", "part = intersect(C, len, na, da, NULL);", "part = intersect(C, len, na, da ? da - 1 : 0, NULL);"),
+    ("recursion-depth", "int st = cnt(g, next, len2, r - 1, levels + 1, &part);", "int st = cnt(g, next, len2, r - 2 > 0 ? r - 2 : 1, levels + 1, &part);"),
+    ("root-level", "st = cnt(p->g, nu, du, p->k - 1, levels, &c);", "st = cnt(p->g, nu, du, p->k, levels, &c);"),
+    ("fill-transposed", "if (degree_before(off, u, cols[e])) dag_cols[pos++] = cols[e];", "if (degree_before(off, cols[e], u)) dag_cols[pos++] = cols[e];"),
+    ("prefix-sum", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u];", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u] - (count[u] > 2);"),
+]
+
+
+def build_mutant(tmp: Path, name: str, a: str, b: str) -> ctypes.CDLL:
+    text = SRC.read_text()
+    assert text.count(a) == 1, name
+    src = tmp / f"m_{name}.c"
+    src.write_text(text.replace(a, b))
+    so = tmp / f"m_{name}.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", str(so), str(src)], check=True)
+    return so
+
+
+def pins_hold() -> bool:
+    """A compact battery of the pins in test_oracle_pins (Fig. 1, closed forms, brute force)."""
+    try:
+        g = gg.fig1()
+        off, cols = oracle.gen_ordering(g.off, g.cols, g.n)
+        arcs = {(u, v) for u in range(g.n) for v in cols[off[u]: off[u + 1]].tolist()}
+        if arcs != {(0, 1), (0, 3), (0, 4), (3, 1), (1, 4), (2, 1), (2, 5), (3, 4), (5, 4), (6, 4), (6, 5)}:
+            return False
+        if [oracle.count_graph(g, k, threads=1) for k in range(1, 6)] != [7, 11, 5, 1, 0]:
+            return False
+        for n in (6, 11):
+            if [oracle.count_graph(gg.complete(n), k, threads=1) for k in range(1, n + 1)] != \
+                    [math.comb(n, k) for k in range(1, n + 1)]:
+                return False
+        parts = [4, 3, 3, 2]
+        g = gg.complete_multipartite(parts)
+        if oracle.count_graph(g, 3, threads=1) != 4 * 3 * 3 + 4 * 3 * 2 + 4 * 3 * 2 + 3 * 3 * 2:
+            return False
+        return True
+    except Exception:
+        return False
+
+
+def test_unmutated_oracle_passes_battery():
+    assert pins_hold()
+
+
+@pytest.mark.parametrize("name,a,b", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, monkeypatch, name, a, b):
+    so = build_mutant(tmp_path, name, a, b)
+    saved = oracle._lib
+    try:
+        oracle._lib = None
+        monkeypatch.setattr(oracle, "_LIB", so)
+        monkeypatch.setattr(oracle, "build", lambda force=False: so)
+        assert not pins_hold(), f"mutant {name} survived the pins"
+    finally:
+        oracle._lib = saved
