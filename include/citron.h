@@ -1,0 +1,152 @@
+/*
+ * citron.h -- C ABI of the GB300 (sm_103a) k-clique counter.
+ *
+ * The method is the ordering-based k-clique counter of "Accelerating Clique Counting in Sparse
+ * Real-World Graphs via Communication-Reducing Optimizations" (CITRON, arXiv 2112.10913):
+ *   ordering phase  -- degree ordering (Sec. II, Sec. IV) and the DAG it induces
+ *                      (Algorithm GenOrdering, Sec. IV);
+ *   counting phase  -- the recursion of Algorithm Counting (Sec. III) over subgraphs induced by
+ *                      out-neighbour sets, built by sorted-set intersection (Sec. V-B), with the
+ *                      prune and the penultimate-level shortcut (Sec. V-B, other optimizations).
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are CSR.  `off` has n+1 uint64 entries (off[0] = 0, non-decreasing), `cols` has
+ *     off[n] uint32 entries, every row sorted strictly ascending.  An undirected input graph
+ *     holds each edge {u,v} as the two arcs u->v and v->u (symmetrised, Sec. VI-B), no self-loops,
+ *     no duplicates (Sec. V-B).  n must be below 2^32 - 1.
+ *   - Pointers named d_* are DEVICE pointers, h_* are HOST pointers.  All memory belongs to the
+ *     caller; the library never allocates, frees or keeps a pointer after a call returns.
+ *   - `ws` is a device workspace of at least citron_workspace_bytes(...) bytes, 256-byte aligned.
+ *     Its contents are scratch: nothing survives from one call to the next.  Two calls that
+ *     overlap in time must not share a workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls that
+ *     return only device results are asynchronous on `stream`; calls that return a host value
+ *     (h_*) synchronise `stream` before returning.
+ *   - Errors are returned, never raised: no abort, no trap, no device assert.  Device kernels
+ *     record the first error in the workspace; the call that owns them reports it.
+ */
+#ifndef CITRON_H
+#define CITRON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CITRON_OK = 0,
+    CITRON_E_INVALID = 1,     /* bad argument or input that breaks the CSR contract */
+    CITRON_E_WORKSPACE = 2,   /* workspace missing, misaligned or smaller than required */
+    CITRON_E_CUDA = 3,        /* a CUDA runtime call failed (launch, copy, sync) */
+    CITRON_E_OVERFLOW = 4,    /* the exact count does not fit in uint64 */
+    CITRON_E_TIMEOUT = 5,     /* a bounded device wait gave up (the result is not valid) */
+    CITRON_E_UNSUPPORTED = 6  /* the input exceeds a documented size limit of this build */
+} citron_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *citron_status_str(citron_status s);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int citron_version(void);
+
+/*
+ * Workspace size in bytes that is enough for every entry point below on a graph with n vertices,
+ * `arcs` = off[n] input arcs and a DAG whose largest out-degree is at most `max_outdeg`
+ * (pass 0 when unknown: the bound min(n-1, arcs/2) is then used, which can be large).
+ */
+size_t citron_workspace_bytes(uint32_t n, uint64_t arcs, uint32_t max_outdeg);
+
+/*
+ * citron_validate -- check the CSR contract on the device: offsets start at 0 and never
+ * decrease, ids < n, rows strictly ascending (sorted, no duplicates), no self-loops, and every
+ * arc u->v has its reverse v->u (symmetrised input, Sec. VI-B).
+ *   returns CITRON_OK or CITRON_E_INVALID; *h_bad (optional) receives a code 1..5 for the first
+ *   kind of defect found (1 offsets, 2 range, 3 order/duplicate, 4 self-loop, 5 asymmetric).
+ * Synchronises `stream`.
+ */
+citron_status citron_validate(uint32_t n, uint64_t arcs, const uint64_t *d_off,
+                              const uint32_t *d_cols, uint32_t *h_bad, void *ws, size_t ws_bytes,
+                              void *stream);
+
+/*
+ * citron_order -- the degree ordering of Sec. II / Sec. IV: vertices sorted by (d(u), u) with
+ * d(u) = off[u+1] - off[u], lower degree first, lower id first on equal degree.
+ *   d_rank[u] (device, n entries, written) = position of u in that order (a permutation);
+ *   d_perm[i] (device, n entries, optional, may be NULL) = the vertex at position i.
+ * Implemented as a stable LSD radix sort of the ids by degree (ids start ascending, so stability
+ * gives the id tie-break).  Asynchronous.
+ */
+citron_status citron_order(uint32_t n, const uint64_t *d_off, uint32_t *d_rank, uint32_t *d_perm,
+                           void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * citron_build_dag -- directionalise the graph (Sec. II) into a DAG in CSR form.
+ *   d_rank == NULL: Algorithm GenOrdering (Sec. IV): the arc u->v is kept iff
+ *       d(u) < d(v) or (d(u) == d(v) and u < v); vertex ids are unchanged and each row keeps the
+ *       input's ascending order.  One fused pass: keep-test, prefix sum and fill.
+ *   d_rank != NULL: any total order given as a permutation rank[0..n): u->v kept iff
+ *       rank[u] < rank[v], and the DAG is RELABELLED: row r belongs to the vertex of rank r and
+ *       holds the ranks of its out-neighbours, sorted ascending.  With the rank of citron_order
+ *       this is the degree-ordered DAG in rank space.  Limit: a row longer than 32768 is reported
+ *       as CITRON_E_UNSUPPORTED (by this call when it synchronises, else by the next one that does).
+ *   Output (device, caller-allocated): d_dag_off[n+1] (uint64), d_dag_cols[arcs/2] (uint32).
+ *   h_max_outdeg (optional host pointer): receives the largest row length of the DAG; when
+ *   given, the call synchronises `stream`, otherwise it is asynchronous.
+ */
+citron_status citron_build_dag(uint32_t n, uint64_t arcs, const uint64_t *d_off,
+                               const uint32_t *d_cols, const uint32_t *d_rank,
+                               uint64_t *d_dag_off, uint32_t *d_dag_cols, uint32_t *h_max_outdeg,
+                               void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * citron_count -- exact number of k-cliques (Sec. II) of the undirected graph whose DAG is given
+ * (any acyclic orientation with sorted rows: the count does not depend on the ordering).
+ *   k = 0 -> CITRON_E_INVALID; k = 1 -> n; k = 2 -> number of arcs of the DAG; k >= 3 -> the
+ *   counting phase (Algorithm Counting with CITRON's subgraphs, Sec. III and Sec. V-B).
+ *   Supported k: 1..CITRON_MAX_K.
+ *   max_outdeg: largest DAG row length if known (from citron_build_dag), else 0 (computed here).
+ *   *h_count (host) receives the count.  A count above 2^64-1 returns CITRON_E_OVERFLOW.
+ *   d_per_root (device, optional, n uint64 entries): when not NULL, receives for every vertex u
+ *   the number of k-cliques whose first vertex in the DAG order is u (for localising errors).
+ * Synchronises `stream`.
+ */
+#define CITRON_MAX_K 12
+citron_status citron_count(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
+                           uint32_t k, uint32_t max_outdeg, uint64_t *h_count,
+                           uint64_t *d_per_root, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * citron_count_tuned -- citron_count with the internal path thresholds exposed (for tests that
+ * must reach every path on small graphs and for the autotuner):
+ *   small_max: roots with out-degree <= small_max use the warp-register path (0..32);
+ *   bitmap_max: roots with out-degree <= bitmap_max use the shared-memory bitmap path
+ *               (small_max < bitmap_max <= 1024); larger roots use the sorted-list path.
+ *   warps_per_cta: warps of the bitmap-path blocks (1..16).
+ * Any argument 0 selects the default.  Same results as citron_count.
+ */
+citron_status citron_count_tuned(uint32_t n, const uint64_t *d_dag_off,
+                                 const uint32_t *d_dag_cols, uint32_t k, uint32_t max_outdeg,
+                                 uint32_t small_max, uint32_t bitmap_max, uint32_t warps_per_cta,
+                                 uint64_t *h_count, uint64_t *d_per_root, void *ws,
+                                 size_t ws_bytes, void *stream);
+
+/*
+ * citron_count_host -- the whole hot path from HOST buffers: copies the CSR (h_off[n+1],
+ * h_cols[arcs]) to the device buffer d_buf, orders (citron_order), builds the relabelled DAG
+ * (citron_build_dag with that rank) and counts every k in h_ks[0..nk) into h_counts[0..nk).
+ * d_buf must hold citron_host_buffer_bytes(n, arcs) bytes; ws as above.  Host buffers should be
+ * pinned for full copy speed (pageable memory works, slower).  Synchronises `stream`.
+ */
+size_t citron_host_buffer_bytes(uint32_t n, uint64_t arcs);
+citron_status citron_count_host(uint32_t n, uint64_t arcs, const uint64_t *h_off,
+                                const uint32_t *h_cols, const uint32_t *h_ks, uint32_t nk,
+                                uint64_t *h_counts, void *d_buf, size_t buf_bytes, void *ws,
+                                size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CITRON_H */

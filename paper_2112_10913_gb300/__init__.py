@@ -1,0 +1,235 @@
+"""GB300 (sm_103a) k-clique counter: the ordering-based method of arXiv 2112.10913 (CITRON).
+
+The compute lives in ``libcitron.so`` (hand-written CUDA, C ABI declared in ``include/citron.h``).
+This module is the thin Python binding: it marshals torch tensors (device memory) and CUDA
+stream handles into the C calls of the same names and turns status codes into exceptions.
+It has no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libcitron.so"
+MAX_K = 12
+
+STATUS = {
+    0: "CITRON_OK",
+    1: "CITRON_E_INVALID",
+    2: "CITRON_E_WORKSPACE",
+    3: "CITRON_E_CUDA",
+    4: "CITRON_E_OVERFLOW",
+    5: "CITRON_E_TIMEOUT",
+    6: "CITRON_E_UNSUPPORTED",
+}
+
+# Every function the C ABI exports (checked against include/citron.h by the tests).
+EXPORTS = (
+    "citron_status_str",
+    "citron_version",
+    "citron_workspace_bytes",
+    "citron_validate",
+    "citron_order",
+    "citron_build_dag",
+    "citron_count",
+    "citron_count_tuned",
+    "citron_host_buffer_bytes",
+    "citron_count_host",
+)
+
+
+class CitronError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        self.name = STATUS.get(code, f"status {code}")
+        super().__init__(f"{where}: {self.name}")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcitron.so (built by ``paper_2112_10913_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"{LIB_PATH} is not built: run paper_2112_10913_gb300.build.build() "
+                           "(needs nvcc); there is no fallback implementation")
+    L = ctypes.CDLL(str(LIB_PATH))
+    vp, u32, u64, sz, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_int
+    L.citron_status_str.argtypes = [i32]
+    L.citron_status_str.restype = ctypes.c_char_p
+    L.citron_version.argtypes = []
+    L.citron_version.restype = i32
+    L.citron_workspace_bytes.argtypes = [u32, u64, u32]
+    L.citron_workspace_bytes.restype = sz
+    L.citron_validate.argtypes = [u32, u64, vp, vp, vp, vp, sz, vp]
+    L.citron_validate.restype = i32
+    L.citron_order.argtypes = [u32, vp, vp, vp, vp, sz, vp]
+    L.citron_order.restype = i32
+    L.citron_build_dag.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.citron_build_dag.restype = i32
+    L.citron_count.argtypes = [u32, vp, vp, u32, u32, vp, vp, vp, sz, vp]
+    L.citron_count.restype = i32
+    L.citron_count_tuned.argtypes = [u32, vp, vp, u32, u32, u32, u32, u32, vp, vp, vp, sz, vp]
+    L.citron_count_tuned.restype = i32
+    L.citron_host_buffer_bytes.argtypes = [u32, u64]
+    L.citron_host_buffer_bytes.restype = sz
+    L.citron_count_host.argtypes = [u32, u64, vp, vp, vp, u32, vp, vp, sz, vp, sz, vp]
+    L.citron_count_host.restype = i32
+    _lib = L
+    return L
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise CitronError(code, where)
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
+# ---------------------------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+
+
+def citron_workspace_bytes(n: int, arcs: int, max_outdeg: int = 0) -> int:
+    return int(lib().citron_workspace_bytes(n, arcs, max_outdeg))
+
+
+def alloc_workspace(n: int, arcs: int, max_outdeg: int = 0, device="cuda"):
+    """Zero-initialised device workspace (uint8 tensor, 256-byte aligned)."""
+    import torch
+
+    ws = torch.zeros(citron_workspace_bytes(n, arcs, max_outdeg) + 256, dtype=torch.uint8, device=device)
+    pad = (-ws.data_ptr()) % 256
+    return ws[pad: pad + ws.numel() - 256]
+
+
+def citron_validate(n: int, off, cols, ws, stream=None) -> int:
+    """0 when the CSR satisfies the input contract, else the smallest defect code (1..5)."""
+    bad = ctypes.c_uint32(0)
+    code = lib().citron_validate(n, int(cols.numel()), _dptr(off), _dptr(cols),
+                                 ctypes.byref(bad), _dptr(ws), _nbytes(ws), _stream(stream))
+    if code not in (0, 1):
+        _check(code, "citron_validate")
+    return int(bad.value)
+
+
+def citron_order(n: int, off, rank, perm=None, ws=None, stream=None):
+    _check(lib().citron_order(n, _dptr(off), _dptr(rank), _dptr(perm), _dptr(ws), _nbytes(ws),
+                              _stream(stream)), "citron_order")
+
+
+def citron_build_dag(n: int, off, cols, rank, dag_off, dag_cols, ws, stream=None,
+                     want_max_outdeg: bool = True):
+    mx = ctypes.c_uint32(0)
+    _check(lib().citron_build_dag(n, int(cols.numel()), _dptr(off), _dptr(cols), _dptr(rank),
+                                  _dptr(dag_off), _dptr(dag_cols),
+                                  ctypes.byref(mx) if want_max_outdeg else ctypes.c_void_p(0),
+                                  _dptr(ws), _nbytes(ws), _stream(stream)), "citron_build_dag")
+    return int(mx.value) if want_max_outdeg else None
+
+
+def citron_count(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, per_root=None,
+                 stream=None, small_max: int = 0, bitmap_max: int = 0, warps_per_cta: int = 0) -> int:
+    out = ctypes.c_uint64(0)
+    if small_max or bitmap_max or warps_per_cta:
+        code = lib().citron_count_tuned(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg,
+                                        small_max, bitmap_max, warps_per_cta, ctypes.byref(out),
+                                        _dptr(per_root), _dptr(ws), _nbytes(ws), _stream(stream))
+    else:
+        code = lib().citron_count(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg,
+                                  ctypes.byref(out), _dptr(per_root), _dptr(ws), _nbytes(ws),
+                                  _stream(stream))
+    _check(code, f"citron_count(k={k})")
+    return int(out.value)
+
+
+def citron_host_buffer_bytes(n: int, arcs: int) -> int:
+    return int(lib().citron_host_buffer_bytes(n, arcs))
+
+
+def citron_count_host(n: int, off: np.ndarray, cols: np.ndarray, ks, d_buf, ws, stream=None) -> list[int]:
+    """Whole path from host CSR arrays (pinned numpy views or torch CPU tensors)."""
+    ks_arr = np.ascontiguousarray(np.asarray(ks, dtype=np.uint32))
+    out = np.zeros(len(ks_arr), dtype=np.uint64)
+    _check(lib().citron_count_host(n, int(cols.shape[0]), ctypes.c_void_p(_host_ptr(off)),
+                                   ctypes.c_void_p(_host_ptr(cols)), ctypes.c_void_p(ks_arr.ctypes.data),
+                                   len(ks_arr), ctypes.c_void_p(out.ctypes.data), _dptr(d_buf),
+                                   _nbytes(d_buf), _dptr(ws), _nbytes(ws), _stream(stream)),
+           "citron_count_host")
+    return [int(x) for x in out]
+
+
+def _host_ptr(a) -> int:
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+# ---------------------------------------------------------------------------------------------
+# Convenience: one graph resident on the device
+
+
+class DeviceGraph:
+    """A CSR graph uploaded once, with its degree ordering and DAG built on the device.
+
+    ``relabel=True`` (default) builds the DAG in rank space from citron_order's ranks;
+    ``relabel=False`` builds the paper's GenOrdering DAG in the input's vertex ids.
+    """
+
+    def __init__(self, g, relabel: bool = True, device="cuda", stream=None, rank=None):
+        import torch
+
+        self.n = g.n
+        self.arcs = int(g.cols.shape[0])
+        dev = torch.device(device)
+        self.off = torch.from_numpy(np.ascontiguousarray(g.off).view(np.int64)).to(dev)
+        self.cols = torch.from_numpy(np.ascontiguousarray(g.cols).view(np.int32)).to(dev)
+        self.ws = alloc_workspace(self.n, self.arcs, 1, device=dev)
+        self.rank = None
+        if rank is not None:
+            self.rank = torch.as_tensor(np.asarray(rank, dtype=np.uint32).view(np.int32), device=dev)
+        elif relabel:
+            self.rank = torch.empty(max(1, self.n), dtype=torch.int32, device=dev)
+            citron_order(self.n, self.off, self.rank, None, self.ws, stream)
+        self.dag_off = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        self.dag_cols = torch.empty(max(1, self.arcs // 2), dtype=torch.int32, device=dev)
+        self.max_outdeg = citron_build_dag(self.n, self.off, self.cols, self.rank, self.dag_off,
+                                           self.dag_cols, self.ws, stream)
+        need = citron_workspace_bytes(self.n, self.arcs, self.max_outdeg)
+        if need > _nbytes(self.ws):
+            self.ws = alloc_workspace(self.n, self.arcs, self.max_outdeg, device=dev)
+
+    def count(self, k: int, per_root=None, stream=None, **tuned) -> int:
+        return citron_count(self.n, self.dag_off, self.dag_cols, k, self.ws, self.max_outdeg,
+                            per_root, stream, **tuned)
+
+    def dag_numpy(self):
+        off = self.dag_off.cpu().numpy().view(np.uint64)
+        cols = self.dag_cols.cpu().numpy().view(np.uint32)[: int(off[-1])]
+        return off, cols

@@ -1,0 +1,279 @@
+// api.cu -- the C ABI (include/citron.h): argument checks, workspace layout, kernel sequencing,
+// error mapping.  Every step of the hot path runs in the kernels of order.cu and count.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "citron.h"
+#include "common.cuh"
+
+namespace citron_host {
+size_t order_ws_bytes(uint32_t n);
+size_t dag_ws_bytes(uint32_t n, uint64_t arcs);
+cudaError_t launch_order(uint32_t n, const uint64_t *off, uint32_t *rank, uint32_t *perm, Carver &c,
+                         cudaStream_t st);
+cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, const uint32_t *cols,
+                             const uint32_t *rank, uint64_t *dag_off, uint32_t *dag_cols,
+                             uint32_t *d_max_outdeg, uint32_t *err, Carver &c, cudaStream_t st,
+                             int num_sms);
+cudaError_t launch_validate(uint32_t n, uint64_t arcs, const uint64_t *off, const uint32_t *cols,
+                            uint32_t *bad, cudaStream_t st, int num_sms);
+size_t count_ws_bytes(uint32_t n, uint32_t max_outdeg, int num_sms);
+cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
+                      uint32_t max_outdeg, const CountPlan &plan, unsigned long long *per_root,
+                      uint32_t *err, Carver &c, cudaStream_t s, int num_sms,
+                      unsigned long long *h_result, uint32_t *h_err);
+cudaError_t launch_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
+                                    unsigned long long *per_root, cudaStream_t s);
+}  // namespace citron_host
+
+using namespace citron_host;
+
+namespace {
+
+// Workspace header: [0] device error word, [1] validation code, [2] max out-degree, rest unused.
+constexpr size_t kHeader = 256;
+
+int sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 132;
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 132;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+uint32_t *err_word(void *ws) { return (uint32_t *)ws; }
+
+citron_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return CITRON_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return CITRON_E_WORKSPACE;
+    }
+    return CITRON_E_CUDA;
+}
+
+citron_status from_device(uint32_t code)
+{
+    switch (code) {
+        case citron::kDevOk: return CITRON_OK;
+        case citron::kDevTimeout: return CITRON_E_TIMEOUT;
+        case citron::kDevOverflow: return CITRON_E_OVERFLOW;
+        case citron::kDevTooLong: return CITRON_E_UNSUPPORTED;
+        case citron::kDevBadInput: return CITRON_E_INVALID;
+        case citron::kDevScratch: return CITRON_E_WORKSPACE;
+        default: return CITRON_E_CUDA;
+    }
+}
+
+bool ws_ok(void *ws, size_t bytes, size_t need)
+{
+    return ws && ((uintptr_t)ws % 256) == 0 && bytes >= need;
+}
+
+// Synchronous calls report (and then clear) the device error word, including errors left by
+// earlier asynchronous calls on the same workspace.
+citron_status finish_sync(void *ws, cudaStream_t s, citron_status st)
+{
+    uint32_t code = 0;
+    cudaError_t e = cudaMemcpyAsync(&code, err_word(ws), sizeof(code), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return CITRON_E_CUDA;
+    if (code) {
+        cudaMemsetAsync(err_word(ws), 0, sizeof(uint32_t), s);
+        cudaStreamSynchronize(s);
+        if (st == CITRON_OK) st = from_device(code);
+    }
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *citron_status_str(citron_status s)
+{
+    switch (s) {
+        case CITRON_OK: return "ok";
+        case CITRON_E_INVALID: return "invalid argument or input";
+        case CITRON_E_WORKSPACE: return "workspace missing, misaligned or too small";
+        case CITRON_E_CUDA: return "CUDA runtime error";
+        case CITRON_E_OVERFLOW: return "count exceeds uint64";
+        case CITRON_E_TIMEOUT: return "bounded device wait gave up";
+        case CITRON_E_UNSUPPORTED: return "input exceeds a size limit of this build";
+    }
+    return "unknown status";
+}
+
+int citron_version(void) { return 100; }
+
+size_t citron_workspace_bytes(uint32_t n, uint64_t arcs, uint32_t max_outdeg)
+{
+    if (max_outdeg == 0) {
+        uint64_t b = arcs / 2;
+        if (n && b > (uint64_t)n - 1) b = (uint64_t)n - 1;
+        max_outdeg = (uint32_t)(b > 0xffffffffull ? 0xffffffffull : b);
+    }
+    size_t need = order_ws_bytes(n);
+    size_t d = dag_ws_bytes(n, arcs);
+    if (d > need) need = d;
+    size_t c = count_ws_bytes(n, max_outdeg, sm_count());
+    if (c > need) need = c;
+    return kHeader + need;
+}
+
+citron_status citron_validate(uint32_t n, uint64_t arcs, const uint64_t *d_off,
+                              const uint32_t *d_cols, uint32_t *h_bad, void *ws, size_t ws_bytes,
+                              void *stream)
+{
+    if (n == 0xffffffffu || !d_off || (arcs && !d_cols)) return CITRON_E_INVALID;
+    if (!ws_ok(ws, ws_bytes, kHeader)) return CITRON_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *bad = err_word(ws) + 1;
+    cudaError_t e = cudaMemsetAsync(bad, 0xff, sizeof(uint32_t), s);
+    if (!e) e = launch_validate(n, arcs, d_off, d_cols, bad, s, sm_count());
+    uint32_t code = 0xffffffffu;
+    if (!e) e = cudaMemcpyAsync(&code, bad, sizeof(code), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return from_cuda(e);
+    if (h_bad) *h_bad = code == 0xffffffffu ? 0 : code;
+    return code == 0xffffffffu ? CITRON_OK : CITRON_E_INVALID;
+}
+
+citron_status citron_order(uint32_t n, const uint64_t *d_off, uint32_t *d_rank, uint32_t *d_perm,
+                           void *ws, size_t ws_bytes, void *stream)
+{
+    if (n == 0xffffffffu || !d_off || (n && !d_rank)) return CITRON_E_INVALID;
+    if (!ws_ok(ws, ws_bytes, kHeader + order_ws_bytes(n))) return CITRON_E_WORKSPACE;
+    Carver c((char *)ws + kHeader, ws_bytes - kHeader);
+    return from_cuda(launch_order(n, d_off, d_rank, d_perm, c, (cudaStream_t)stream));
+}
+
+citron_status citron_build_dag(uint32_t n, uint64_t arcs, const uint64_t *d_off,
+                               const uint32_t *d_cols, const uint32_t *d_rank,
+                               uint64_t *d_dag_off, uint32_t *d_dag_cols, uint32_t *h_max_outdeg,
+                               void *ws, size_t ws_bytes, void *stream)
+{
+    if (n == 0xffffffffu || !d_off || !d_dag_off || (arcs && (!d_cols || !d_dag_cols)) ||
+        (arcs & 1))
+        return CITRON_E_INVALID;
+    if (!ws_ok(ws, ws_bytes, kHeader + dag_ws_bytes(n, arcs))) return CITRON_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *d_max = h_max_outdeg ? err_word(ws) + 2 : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (d_max) e = cudaMemsetAsync(d_max, 0, sizeof(uint32_t), s);
+    Carver c((char *)ws + kHeader, ws_bytes - kHeader);
+    if (!e)
+        e = launch_build_dag(n, arcs, d_off, d_cols, d_rank, d_dag_off, d_dag_cols, d_max,
+                             err_word(ws), c, s, sm_count());
+    if (e) return from_cuda(e);
+    if (!h_max_outdeg) return CITRON_OK;
+    e = cudaMemcpyAsync(h_max_outdeg, d_max, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e) return from_cuda(e);
+    return finish_sync(ws, s, CITRON_OK);
+}
+
+citron_status citron_count_tuned(uint32_t n, const uint64_t *d_dag_off,
+                                 const uint32_t *d_dag_cols, uint32_t k, uint32_t max_outdeg,
+                                 uint32_t small_max, uint32_t bitmap_max, uint32_t warps_per_cta,
+                                 uint64_t *h_count, uint64_t *d_per_root, void *ws,
+                                 size_t ws_bytes, void *stream)
+{
+    if (!h_count || !d_dag_off || n == 0xffffffffu || k == 0) return CITRON_E_INVALID;
+    if (k > CITRON_MAX_K) return CITRON_E_UNSUPPORTED;
+    if (small_max > 32 || bitmap_max > 1024 || warps_per_cta > 16) return CITRON_E_INVALID;
+    CountPlan plan;
+    if (small_max) plan.small_max = small_max;
+    if (bitmap_max) plan.bitmap_max = bitmap_max;
+    if (warps_per_cta) plan.warps_per_cta = warps_per_cta;
+    if (plan.bitmap_max < plan.small_max) plan.bitmap_max = plan.small_max;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ws_ok(ws, ws_bytes, kHeader)) return CITRON_E_WORKSPACE;
+    unsigned long long *per_root = (unsigned long long *)d_per_root;
+    if (k <= 2) {
+        cudaError_t e = cudaSuccess;
+        if (k == 1) {
+            *h_count = n;
+        } else {
+            uint64_t m = 0;
+            e = cudaMemcpyAsync(&m, d_dag_off + n, sizeof(m), cudaMemcpyDeviceToHost, s);
+            if (!e) e = cudaStreamSynchronize(s);
+            *h_count = m;
+        }
+        if (!e && per_root) e = launch_per_root_trivial(n, d_dag_off, k, per_root, s);
+        if (e) return from_cuda(e);
+        return finish_sync(ws, s, CITRON_OK);
+    }
+    if (n && !d_dag_cols) return CITRON_E_INVALID;
+    Carver c((char *)ws + kHeader, ws_bytes - kHeader);
+    unsigned long long result = 0;
+    uint32_t dev_err = 0;
+    cudaError_t e = run_count(n, d_dag_off, d_dag_cols, k, max_outdeg, plan, per_root,
+                              err_word(ws), c, s, sm_count(), &result, &dev_err);
+    if (e) return from_cuda(e);
+    citron_status st = finish_sync(ws, s, CITRON_OK);
+    if (st == CITRON_OK) *h_count = result;
+    return st;
+}
+
+citron_status citron_count(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
+                           uint32_t k, uint32_t max_outdeg, uint64_t *h_count,
+                           uint64_t *d_per_root, void *ws, size_t ws_bytes, void *stream)
+{
+    return citron_count_tuned(n, d_dag_off, d_dag_cols, k, max_outdeg, 0, 0, 0, h_count,
+                              d_per_root, ws, ws_bytes, stream);
+}
+
+size_t citron_host_buffer_bytes(uint32_t n, uint64_t arcs)
+{
+    Sizer z;
+    z.take<uint64_t>((size_t)n + 1);  // off
+    z.take<uint32_t>(arcs + 1);       // cols
+    z.take<uint32_t>((size_t)n + 1);  // rank
+    z.take<uint64_t>((size_t)n + 1);  // dag_off
+    z.take<uint32_t>(arcs / 2 + 1);   // dag_cols
+    return z.used;
+}
+
+citron_status citron_count_host(uint32_t n, uint64_t arcs, const uint64_t *h_off,
+                                const uint32_t *h_cols, const uint32_t *h_ks, uint32_t nk,
+                                uint64_t *h_counts, void *d_buf, size_t buf_bytes, void *ws,
+                                size_t ws_bytes, void *stream)
+{
+    if (n == 0xffffffffu || !h_off || (arcs && !h_cols) || (nk && (!h_ks || !h_counts)))
+        return CITRON_E_INVALID;
+    if (!d_buf || buf_bytes < citron_host_buffer_bytes(n, arcs)) return CITRON_E_WORKSPACE;
+    Carver b(d_buf, buf_bytes);
+    uint64_t *off = b.take<uint64_t>((size_t)n + 1);
+    uint32_t *cols = b.take<uint32_t>(arcs + 1);
+    uint32_t *rank = b.take<uint32_t>((size_t)n + 1);
+    uint64_t *dag_off = b.take<uint64_t>((size_t)n + 1);
+    uint32_t *dag_cols = b.take<uint32_t>(arcs / 2 + 1);
+    if (!b.ok) return CITRON_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(off, h_off, ((size_t)n + 1) * sizeof(uint64_t),
+                                    cudaMemcpyHostToDevice, s);
+    if (!e && arcs) e = cudaMemcpyAsync(cols, h_cols, arcs * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    if (e) return from_cuda(e);
+    citron_status st = citron_order(n, off, rank, nullptr, ws, ws_bytes, stream);
+    if (st) return st;
+    uint32_t max_outdeg = 0;
+    st = citron_build_dag(n, arcs, off, cols, rank, dag_off, dag_cols, &max_outdeg, ws, ws_bytes,
+                          stream);
+    if (st) return st;
+    for (uint32_t i = 0; i < nk; i++) {
+        st = citron_count(n, dag_off, dag_cols, h_ks[i], max_outdeg, &h_counts[i], nullptr, ws,
+                          ws_bytes, stream);
+        if (st) return st;
+    }
+    return CITRON_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// common.cuh -- internal helpers of the CUDA path (not part of the C ABI).
+//
+// Device-side error reporting, the workspace carver, warp/block scans and the decoupled
+// look-back tile prefix used by the single-pass compaction and scan kernels.
+#pragma once
+
+#include <cuda/atomic>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "citron.h"
+
+namespace citron {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+// Device error word layout (first 64 bytes of every workspace): word 0 = first error code.
+enum DevErr : uint32_t {
+    kDevOk = 0,
+    kDevTimeout = 1,      // a bounded spin gave up
+    kDevOverflow = 2,     // a uint64 sum wrapped
+    kDevTooLong = 3,      // a row exceeded a compiled capacity
+    kDevBadInput = 4,     // input violated the CSR contract where the kernel checks it
+    kDevScratch = 5,      // workspace sized for a smaller max out-degree than the input has
+};
+
+__device__ __forceinline__ void set_error(uint32_t *err, uint32_t code)
+{
+    atomicCAS(err, 0u, code);
+}
+
+// Spin limit for every device wait (decoupled look-back).  Each probe is an L2 round trip
+// (~1 us under load), so the limit bounds a wait to a few seconds at most.
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Exact uint64 accumulation into a global counter; flags a wrap past 2^64 - 1.
+__device__ __forceinline__ void add_checked(unsigned long long *dst, unsigned long long v,
+                                            uint32_t *err)
+{
+    if (v == 0) return;
+    unsigned long long old = atomicAdd(dst, v);
+    if (old + v < old) set_error(err, kDevOverflow);
+}
+
+// Warp sum of uint64 lane values with wrap detection.
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v, uint32_t *err)
+{
+    bool wrapped = false;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(kFull, v, o);
+        unsigned long long s = v + w;
+        wrapped |= s < v;
+        v = s;
+    }
+    if (__any_sync(kFull, wrapped) && (threadIdx.x & 31) == 0) set_error(err, kDevOverflow);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Inclusive warp scan (uint32).
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive block scan of one uint32 per thread; returns the exclusive prefix and the total.
+// `scratch` needs blockDim.x / 32 + 1 words.  Contains __syncthreads.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch, uint32_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t incl = warp_incl_scan(v);
+    if (lane == 31) scratch[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < nw ? scratch[lane] : 0;
+        uint32_t si = warp_incl_scan(s);
+        if (lane < nw) scratch[lane] = si - s;
+        if (lane == nw - 1) scratch[nw] = si;
+    }
+    __syncthreads();
+    uint32_t r = scratch[warp] + incl - v;
+    total = scratch[nw];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Decoupled look-back (single-pass prefix over tiles).  status[t] packs a 2-bit flag and a 62-bit
+// value: flag 1 = the tile's own aggregate is published, flag 2 = its inclusive prefix is.
+// Tiles take ids from an atomic ticket in launch order, so a tile only ever waits on tiles that
+// are already running; every wait is bounded by kSpinLimit and reports kDevTimeout.
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ void publish(unsigned long long *status, uint32_t t,
+                                        unsigned long long v)
+{
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> ref(status[t]);
+    ref.store(v, cuda::memory_order_release);
+}
+
+__device__ __forceinline__ unsigned long long peek(unsigned long long *status, long long t)
+{
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> ref(status[t]);
+    return ref.load(cuda::memory_order_acquire);
+}
+
+// Called by ONE full warp of the tile's block.  Returns the exclusive prefix of tile t and
+// publishes its inclusive prefix.  `agg` must be the same on all lanes.
+__device__ __forceinline__ unsigned long long lookback_warp(unsigned long long *status, uint32_t t,
+                                                            unsigned long long agg, uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    if (t == 0) {
+        if (lane == 0) publish(status, 0, kFlagPre | agg);
+        return 0;
+    }
+    if (lane == 0) publish(status, t, kFlagAgg | agg);
+    unsigned long long excl = 0;
+    long long j = (long long)t - 1;
+    uint32_t spins = 0;
+    while (true) {
+        long long idx = j - lane;
+        unsigned long long s = idx >= 0 ? peek(status, idx) : kFlagPre;
+        unsigned long long flag = s & ~kValMask;
+        uint32_t pre = __ballot_sync(kFull, flag == kFlagPre);
+        uint32_t zero = __ballot_sync(kFull, flag == 0);
+        uint32_t upto = pre ? ((__ffs(pre) == 32) ? kFull : ((1u << __ffs(pre)) - 1)) : kFull;
+        if (zero & upto) {
+            if (++spins > kSpinLimit) {
+                if (lane == 0) set_error(err, kDevTimeout);
+                break;
+            }
+            continue;
+        }
+        unsigned long long v = (upto >> lane) & 1 ? (s & kValMask) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        excl += v;
+        if (pre) break;
+        j -= 32;
+    }
+    if (lane == 0) publish(status, t, kFlagPre | ((excl + agg) & kValMask));
+    return excl;
+}
+
+}  // namespace citron
+
+// ---------------------------------------------------------------------------------------------
+// Host side: workspace carving (every region 256-byte aligned).
+
+namespace citron_host {
+
+// Path thresholds of the counting phase (see count.cu).
+struct CountPlan {
+    uint32_t small_max = 32;       // roots with out-degree <= this use the warp-register path
+    uint32_t bitmap_max = 1024;    // ... <= this use the shared-memory bitmap path
+    uint32_t warps_per_cta = 16;   // warps per block of the bitmap path
+};
+
+struct Carver {
+    char *base;
+    size_t cap;
+    size_t used = 0;
+    bool ok = true;
+    Carver(void *p, size_t bytes) : base((char *)p), cap(bytes) {}
+    template <class T>
+    T *take(size_t count)
+    {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (used + bytes > cap || !base) {
+            ok = false;
+            used += bytes;
+            return nullptr;
+        }
+        T *p = (T *)(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+// Size-only twin of Carver used by the *_bytes queries.
+struct Sizer {
+    size_t used = 0;
+    template <class T>
+    void take(size_t count) { used += (count * sizeof(T) + 255) & ~size_t(255); }
+};
+
+}  // namespace citron_host

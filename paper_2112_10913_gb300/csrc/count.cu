@@ -1,0 +1,593 @@
+// count.cu -- counting phase on sm_103a (Algorithm Counting, Sec. III, with CITRON's subgraphs,
+// Sec. V-B).
+//
+// Every k-clique is counted once, at its first vertex u in the DAG order ("root"), as a
+// (k-1)-clique of the subgraph induced by N+(u) (Sec. II: g_u with V(g_u) = N+(u)).  Roots with
+// fewer than k-1 out-neighbours are skipped (the prune of Sec. V-B).  Roots are split by their
+// out-degree D:
+//   D <= small_max (<= 32)  k_count_small: one warp per root.  Row i of the local subgraph
+//       (V(g_u) ∩ N+(a_i), Algorithm GenSubgraph of CITRON) is a 32-bit mask held by lane i.  The
+//       recursion runs warp-uniform on candidate masks; the penultimate level adds subgraph
+//       degrees for all candidates in one step (Counting's l = 2 branch, Sec. V-B last paragraph).
+//   D <= bitmap_max (<= 1024) k_count_mid: one block per root, roots taken largest-D first from
+//       a device queue.  The local subgraph is a D x D bitmap in shared memory built by
+//       intersecting the sorted list N+(u) with every N+(a_i) (binary search of each element of
+//       N+(a_i) in N+(u), lists kept sorted as in the paper).  Its edges (u, a_i) are the tasks
+//       of the block's warps (edge-parallel counting); a warp recurses with the candidate set
+//       spread over its lanes, one 32-bit word per lane, using ballot / popc / shuffles.
+//   D > bitmap_max  k_count_list: one warp per root, candidate sets kept as sorted lists in
+//       global scratch, intersections by binary search (the sorted-list form of Sec. V-B).
+// Counts are exact uint64; every addition into a shared total checks for wrap-around.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace citron {
+
+constexpr int kMaxK = CITRON_MAX_K;
+constexpr uint32_t kBitmapCap = 1024;  // largest root handled by the bitmap path
+constexpr int kSmallWarps = 8;         // warps per block of k_count_small
+constexpr int kListWarps = 4;          // warps per block of k_count_list
+
+struct CountStats {
+    uint32_t n_small, n_mid, n_big;
+    uint32_t max_mid, max_big, max_all;
+    uint32_t pad[2];
+};
+
+// ------------------------------------------------------------------------------------------
+// Root classification.
+
+__global__ void k_classify(uint32_t n, const uint64_t *__restrict__ dag_off, uint32_t need,
+                           uint32_t small_max, uint32_t bitmap_max, uint32_t *small_list,
+                           uint32_t *big_list, uint32_t *mid_hist, CountStats *st,
+                           unsigned long long *per_root)
+{
+    __shared__ uint32_t s_cnt[2], s_base[2], s_max[3];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x < 3) s_max[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t D = 0;
+    int cls = -1;  // 0 small, 1 big, 2 mid
+    if (u < n) {
+        const uint64_t d64 = dag_off[u + 1] - dag_off[u];
+        D = (uint32_t)min(d64, (uint64_t)0xffffffffull);
+        if (per_root) per_root[u] = 0;
+        if (D >= need) cls = D <= small_max ? 0 : (D <= bitmap_max ? 2 : 1);
+    }
+    uint32_t off_in_warp[2] = {0, 0}, warp_base[2] = {0, 0};
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const uint32_t bal = __ballot_sync(kFull, cls == c);
+        off_in_warp[c] = __popc(bal & lanemask_lt());
+        if (bal && lane == 0) warp_base[c] = atomicAdd(&s_cnt[c], __popc(bal));
+        warp_base[c] = __shfl_sync(kFull, warp_base[c], 0);
+    }
+    if (cls == 2) atomicAdd(&mid_hist[D], 1u);
+    uint32_t m = D;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    if (lane == 0 && m) atomicMax(&s_max[2], m);
+    if (cls == 2) atomicMax(&s_max[0], D);
+    if (cls == 1) atomicMax(&s_max[1], D);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_base[0] = s_cnt[0] ? atomicAdd(&st->n_small, s_cnt[0]) : 0;
+        s_base[1] = s_cnt[1] ? atomicAdd(&st->n_big, s_cnt[1]) : 0;
+        if (s_max[0]) atomicMax(&st->max_mid, s_max[0]);
+        if (s_max[1]) atomicMax(&st->max_big, s_max[1]);
+        if (s_max[2]) atomicMax(&st->max_all, s_max[2]);
+    }
+    __syncthreads();
+    if (cls == 0) small_list[s_base[0] + warp_base[0] + off_in_warp[0]] = u;
+    if (cls == 1) big_list[s_base[1] + warp_base[1] + off_in_warp[1]] = u;
+}
+
+// Bin starts for the mid roots in DESCENDING out-degree: cursor[d] = #roots with degree > d.
+__global__ __launch_bounds__(1024) void k_mid_bins(const uint32_t *hist, uint32_t bins,
+                                                    uint32_t *cursor, CountStats *st)
+{
+    __shared__ uint32_t scratch[33];
+    // reversed index: position i holds degree bins-1-i
+    const uint32_t per = (bins + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(bins, threadIdx.x * per), hi = min(bins, lo + per);
+    uint32_t s = 0;
+    for (uint32_t i = lo; i < hi; i++) s += hist[bins - 1 - i];
+    uint32_t total;
+    uint32_t run = block_excl_scan(s, scratch, total);
+    for (uint32_t i = lo; i < hi; i++) {
+        const uint32_t d = bins - 1 - i;
+        cursor[d] = run;
+        run += hist[d];
+    }
+    if (threadIdx.x == 0) st->n_mid = total;
+}
+
+__global__ void k_mid_scatter(uint32_t n, const uint64_t *__restrict__ dag_off, uint32_t need,
+                              uint32_t small_max, uint32_t bitmap_max, uint32_t *cursor,
+                              uint32_t *mid_list)
+{
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t D = 0xffffffffu;
+    if (u < n) {
+        const uint64_t d64 = dag_off[u + 1] - dag_off[u];
+        if (d64 >= need && d64 > small_max && d64 <= bitmap_max) D = (uint32_t)d64;
+    }
+    const uint32_t peers = __match_any_sync(kFull, D);
+    if (D == 0xffffffffu) return;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if ((threadIdx.x & 31) == leader) base = atomicAdd(&cursor[D], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    mid_list[base + __popc(peers & lanemask_lt())] = u;
+}
+
+// ------------------------------------------------------------------------------------------
+// Warp-register path (D <= 32).
+
+// Number of R-cliques inside the warp-uniform candidate mask `cand` (bit j = j-th out-neighbour
+// of the root); lane i holds row i of the local subgraph.  Adds lane-partial sums to acc.
+template <int R>
+__device__ __forceinline__ void small_dfs(uint32_t cand, uint32_t myrow, int lane,
+                                          unsigned long long &acc)
+{
+    if constexpr (R == 1) {
+        if (lane == 0) acc += __popc(cand);
+    } else if constexpr (R == 2) {
+        if ((cand >> lane) & 1) acc += __popc(cand & myrow);
+    } else {
+        uint32_t c = cand;
+        while (c) {
+            const int a = __ffs(c) - 1;
+            c &= c - 1;
+            const uint32_t c2 = cand & __shfl_sync(kFull, myrow, a);
+            if (__popc(c2) >= R - 1) small_dfs<R - 1>(c2, myrow, lane, acc);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t lower_bound_smem(const uint32_t *a, uint32_t n, uint32_t x)
+{
+    uint32_t lo = 0, len = n;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if (a[lo + half] < x) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
+template <int K>
+__global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
+    const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
+    const uint32_t *__restrict__ list, const CountStats *st, unsigned long long *result,
+    unsigned long long *per_root, uint32_t *err)
+{
+    __shared__ uint32_t sL[kSmallWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t nlist = st->n_small;
+    const uint32_t gw = blockIdx.x * kSmallWarps + w, nwarps = gridDim.x * kSmallWarps;
+    unsigned long long total = 0;
+    for (uint32_t idx = gw; idx < nlist; idx += nwarps) {
+        const uint32_t u = list[idx];
+        const uint64_t base = dag_off[u];
+        const uint32_t D = (uint32_t)(dag_off[u + 1] - base);
+        const uint32_t x = lane < D ? dag_cols[base + lane] : 0xffffffffu;
+        sL[w][lane] = x;
+        __syncwarp();
+        const uint32_t lmax = __shfl_sync(kFull, x, D - 1);
+        uint64_t rb = 0, re = 0;
+        if (lane < D) {
+            rb = dag_off[x];
+            re = dag_off[x + 1];
+        }
+        uint32_t myrow = 0;
+        for (uint32_t i = 0; i < D; i++) {
+            const uint64_t b = __shfl_sync(kFull, rb, i), e = __shfl_sync(kFull, re, i);
+            uint32_t bits = 0;
+            for (uint64_t p = b; p < e; p += 32) {
+                const uint32_t y = p + lane < e ? dag_cols[p + lane] : 0xffffffffu;
+                if (__shfl_sync(kFull, y, 0) > lmax) break;
+                if (y <= lmax) {
+                    const uint32_t j = lower_bound_smem(sL[w], D, y);
+                    if (sL[w][j] == y) bits |= 1u << j;
+                }
+            }
+            bits = __reduce_or_sync(kFull, bits);
+            if (lane == i) myrow = bits;
+        }
+        unsigned long long acc = 0;
+        const uint32_t all = D == 32 ? kFull : ((1u << D) - 1);
+        small_dfs<K - 1>(all, myrow, lane, acc);
+        if (per_root) {
+            const unsigned long long r = warp_sum_u64(acc, err);
+            if (lane == 0) per_root[u] = r;
+        }
+        total += acc;
+        __syncwarp();
+    }
+    total = warp_sum_u64(total, err);
+    if (lane == 0) add_checked(result, total, err);
+}
+
+// ------------------------------------------------------------------------------------------
+// Shared-memory bitmap path (small_max < D <= 1024).
+
+// Lane l holds word l of the candidate set (words >= W are zero).  Adds lane-partial counts of
+// the R-cliques inside the candidate set to acc.
+template <int R>
+__device__ __forceinline__ void warp_dfs(const uint32_t *rows, uint32_t RS, uint32_t W, uint32_t c,
+                                         int lane, unsigned long long &acc)
+{
+    if constexpr (R == 1) {
+        acc += __popc(c);
+    } else if constexpr (R == 2) {
+        const uint32_t nzw = __ballot_sync(kFull, c != 0);
+        uint32_t outer = nzw;
+        uint32_t s = 0;
+        while (outer) {
+            const int w = __ffs(outer) - 1;
+            outer &= outer - 1;
+            const uint32_t cw = __shfl_sync(kFull, c, w);
+            const bool act = (cw >> lane) & 1;
+            const uint32_t *row = rows + (size_t)(w * 32 + lane) * RS;
+            uint32_t inner = nzw;
+            while (inner) {
+                const int w2 = __ffs(inner) - 1;
+                inner &= inner - 1;
+                const uint32_t v = __shfl_sync(kFull, c, w2);
+                if (act) s += __popc(v & row[w2]);
+            }
+        }
+        acc += s;
+    } else {
+        uint32_t rem = c;
+        for (;;) {
+            const uint32_t nz = __ballot_sync(kFull, rem != 0);
+            if (!nz) break;
+            const int wl = __ffs(nz) - 1;
+            const uint32_t word = __shfl_sync(kFull, rem, wl);
+            const uint32_t a = wl * 32 + __ffs(word) - 1;
+            if (lane == wl) rem &= rem - 1;
+            const uint32_t c2 = lane < W ? (c & rows[a * RS + lane]) : 0u;
+            const uint32_t cnt = __reduce_add_sync(kFull, __popc(c2));
+            if (cnt >= R - 1) warp_dfs<R - 1>(rows, RS, W, c2, lane, acc);
+        }
+    }
+}
+
+constexpr int kMidMaxWarps = 16;
+
+template <int K>
+__global__ __launch_bounds__(kMidMaxWarps * 32) void k_count_mid(const uint64_t *__restrict__ dag_off,
+                            const uint32_t *__restrict__ dag_cols, const uint32_t *__restrict__ list,
+                            const CountStats *st, uint32_t *next, uint32_t dcap,
+                            unsigned long long *result, unsigned long long *per_root,
+                            uint32_t *err)
+{
+    extern __shared__ uint32_t smem[];
+    uint32_t *sL = smem;
+    uint32_t *rows = smem + dcap;
+    __shared__ uint32_t s_idx, s_task;
+    __shared__ unsigned long long s_acc[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t nlist = st->n_mid;
+    unsigned long long block_total = 0;  // meaningful in thread 0
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_idx = atomicAdd(next, 1u);
+            s_task = 0;
+        }
+        __syncthreads();
+        const uint32_t idx = s_idx;
+        if (idx >= nlist) break;
+        const uint32_t u = list[idx];
+        const uint64_t base = dag_off[u];
+        const uint32_t D = (uint32_t)(dag_off[u + 1] - base);
+        const uint32_t W = (D + 31) >> 5, RS = W | 1;
+        for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) sL[i] = dag_cols[base + i];
+        if (K > 3)
+            for (uint32_t i = threadIdx.x; i < D * RS; i += blockDim.x) rows[i] = 0;
+        __syncthreads();
+        const uint32_t lmax = sL[D - 1];
+        unsigned long long acc = 0;
+        // Build the local subgraph: row i = V(g_u) ∩ N+(a_i) (CITRON's GenSubgraph).
+        for (uint32_t i = w; i < D; i += nw) {
+            const uint32_t a = sL[i];
+            const uint64_t b = dag_off[a], e = dag_off[a + 1];
+            for (uint64_t p = b; p < e; p += 32) {
+                const uint32_t y = p + lane < e ? dag_cols[p + lane] : 0xffffffffu;
+                if (__shfl_sync(kFull, y, 0) > lmax) break;
+                if (y <= lmax) {
+                    const uint32_t j = lower_bound_smem(sL, D, y);
+                    if (sL[j] == y) {
+                        if (K == 3) acc += 1;
+                        else atomicOr(&rows[i * RS + (j >> 5)], 1u << (j & 31));
+                    }
+                }
+            }
+        }
+        if (K > 3) {
+            __syncthreads();
+            // Edge tasks (u, a_t): count (K-2)-cliques in row t.
+            for (;;) {
+                uint32_t t = 0;
+                if (lane == 0) t = atomicAdd(&s_task, 1u);
+                t = __shfl_sync(kFull, t, 0);
+                if (t >= D) break;
+                const uint32_t c = lane < W ? rows[t * RS + lane] : 0u;
+                const uint32_t cnt = __reduce_add_sync(kFull, __popc(c));
+                if (cnt >= K - 2) warp_dfs<K - 2>(rows, RS, W, c, lane, acc);
+            }
+        }
+        const unsigned long long ws = warp_sum_u64(acc, err);
+        if (lane == 0) s_acc[w] = ws;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long r = 0;
+            bool wrapped = false;
+            for (int i = 0; i < nw; i++) {
+                const unsigned long long s = r + s_acc[i];
+                wrapped |= s < r;
+                r = s;
+            }
+            if (wrapped) set_error(err, kDevOverflow);
+            if (per_root) per_root[u] = r;
+            const unsigned long long s = block_total + r;
+            if (s < block_total) set_error(err, kDevOverflow);
+            block_total = s;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) add_checked(result, block_total, err);
+}
+
+// ------------------------------------------------------------------------------------------
+// Sorted-list path (D > bitmap_max).
+
+// R-cliques inside the sorted candidate list C[0..len); buf holds one list per deeper level.
+template <int R>
+__device__ void list_dfs(const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ cols,
+                         const uint32_t *C, uint32_t len, uint32_t *buf, uint32_t stride, int lane,
+                         unsigned long long &acc)
+{
+    if (len < (uint32_t)R) return;
+    if constexpr (R == 1) {
+        if (lane == 0) acc += len;
+    } else {
+        for (uint32_t i = 0; i < len; i++) {
+            const uint32_t a = C[i];
+            const uint64_t ab = dag_off[a], ae = dag_off[a + 1];
+            uint32_t out = 0;
+            for (uint32_t p = 0; p < len; p += 32) {
+                bool hit = false;
+                uint32_t x = 0;
+                if (p + lane < len) {
+                    x = C[p + lane];
+                    uint64_t lo = ab, hi = ae;
+                    while (lo < hi) {
+                        const uint64_t mid = lo + (hi - lo) / 2;
+                        if (cols[mid] < x) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    hit = lo < ae && cols[lo] == x;
+                }
+                const uint32_t bal = __ballot_sync(kFull, hit);
+                if constexpr (R == 2) {
+                    if (lane == 0) acc += __popc(bal);
+                } else {
+                    if (hit) buf[out + __popc(bal & lanemask_lt())] = x;
+                }
+                out += __popc(bal);
+            }
+            if constexpr (R >= 3) {
+                __syncwarp();
+                if (out >= (uint32_t)(R - 1))
+                    list_dfs<R - 1>(dag_off, cols, buf, out, buf + stride, stride, lane, acc);
+                __syncwarp();
+            }
+        }
+    }
+}
+
+template <int K>
+__global__ __launch_bounds__(kListWarps * 32) void k_count_list(
+    const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
+    const uint32_t *__restrict__ list, const CountStats *st, uint32_t *next, uint32_t *scratch,
+    uint32_t stride, unsigned long long *result, unsigned long long *per_root, uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = blockIdx.x * kListWarps + (threadIdx.x >> 5);
+    uint32_t *buf = scratch + (size_t)gw * stride * (K > 3 ? K - 3 : 1);
+    const uint32_t nlist = st->n_big;
+    unsigned long long total = 0;
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(next, 1u);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= nlist) break;
+        const uint32_t u = list[idx];
+        const uint64_t base = dag_off[u];
+        const uint32_t D = (uint32_t)(dag_off[u + 1] - base);
+        if (D > stride) {
+            if (lane == 0) set_error(err, kDevScratch);
+            continue;
+        }
+        unsigned long long acc = 0;
+        list_dfs<K - 1>(dag_off, dag_cols, dag_cols + base, D, buf, stride, lane, acc);
+        if (per_root) {
+            const unsigned long long r = warp_sum_u64(acc, err);
+            if (lane == 0) per_root[u] = r;
+        }
+        total += acc;
+    }
+    total = warp_sum_u64(total, err);
+    if (lane == 0) add_checked(result, total, err);
+}
+
+__global__ void k_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
+                                   unsigned long long *per_root)
+{
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) per_root[u] = k == 1 ? 1ull : (unsigned long long)(dag_off[u + 1] - dag_off[u]);
+}
+
+}  // namespace citron
+
+// ------------------------------------------------------------------------------------------
+// Host side.
+
+namespace citron_host {
+
+using namespace citron;
+
+size_t count_ws_bytes(uint32_t n, uint32_t max_outdeg, int num_sms)
+{
+    Sizer s;
+    s.take<CountStats>(1);
+    s.take<unsigned long long>(2);
+    s.take<uint32_t>(8);                      // queue counters
+    s.take<uint32_t>((size_t)n + 1);          // small list
+    s.take<uint32_t>((size_t)n + 1);          // mid list
+    s.take<uint32_t>((size_t)n + 1);          // big list
+    s.take<uint32_t>(kBitmapCap + 2);         // mid histogram
+    s.take<uint32_t>(kBitmapCap + 2);         // mid cursors
+    const uint32_t list_warps = (uint32_t)num_sms * kListWarps;
+    const size_t stride = max_outdeg > kBitmapCap ? max_outdeg : 0;
+    s.take<uint32_t>(stride * list_warps * (kMaxK - 3) + 1);
+    return s.used;
+}
+
+template <int K>
+static cudaError_t launch_count_k(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols,
+                                  const CountPlan &plan, const CountStats &hs, const CountStats *st,
+                                  const uint32_t *small_list, const uint32_t *mid_list,
+                                  const uint32_t *big_list, uint32_t *next, uint32_t *list_scratch,
+                                  size_t list_scratch_words, unsigned long long *result,
+                                  unsigned long long *per_root, uint32_t *err, cudaStream_t s,
+                                  int num_sms)
+{
+    cudaError_t e = cudaSuccess;
+    if (hs.n_mid) {
+        const uint32_t dcap = (hs.max_mid + 31) & ~31u;
+        const uint32_t rs = (dcap / 32) | 1;
+        const size_t smem = ((size_t)dcap + (K > 3 ? (size_t)dcap * rs : 0)) * sizeof(uint32_t);
+        const int threads = plan.warps_per_cta * 32;
+        if ((e = cudaFuncSetAttribute(k_count_mid<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)))
+            return e;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_mid<K>, threads,
+                                                               smem)))
+            return e;
+        if (per_sm < 1) per_sm = 1;
+        uint32_t grid = (uint32_t)(num_sms * per_sm);
+        if (grid > hs.n_mid) grid = hs.n_mid;
+        k_count_mid<K><<<grid, threads, smem, s>>>(dag_off, dag_cols, mid_list, st, next + 0, dcap,
+                                                   result, per_root, err);
+        if ((e = cudaGetLastError())) return e;
+    }
+    if (hs.n_small) {
+        uint32_t grid = (hs.n_small + kSmallWarps - 1) / kSmallWarps;
+        const uint32_t cap = (uint32_t)num_sms * 16;
+        if (grid > cap) grid = cap;
+        k_count_small<K><<<grid, kSmallWarps * 32, 0, s>>>(dag_off, dag_cols, small_list, st, result,
+                                                           per_root, err);
+        if ((e = cudaGetLastError())) return e;
+    }
+    if (hs.n_big) {
+        const size_t per_warp = (size_t)hs.max_big * (K > 3 ? K - 3 : 1);
+        size_t warps = per_warp ? list_scratch_words / per_warp : 0;
+        if (warps < kListWarps) return cudaErrorMemoryAllocation;
+        uint32_t grid = (uint32_t)(warps / kListWarps);
+        const uint32_t cap = (uint32_t)num_sms;
+        if (grid > cap) grid = cap;
+        if (grid > (hs.n_big + kListWarps - 1) / kListWarps) grid = (hs.n_big + kListWarps - 1) / kListWarps;
+        k_count_list<K><<<grid, kListWarps * 32, 0, s>>>(dag_off, dag_cols, big_list, st, next + 1,
+                                                         list_scratch, hs.max_big, result, per_root,
+                                                         err);
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
+// Runs the count for k >= 3.  Returns a CUDA error, or cudaErrorMemoryAllocation when the
+// workspace is too small.  The host value lands in *h_result; device errors in *h_err.
+cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
+                      uint32_t max_outdeg, const CountPlan &plan, unsigned long long *per_root,
+                      uint32_t *err, Carver &c, cudaStream_t s, int num_sms,
+                      unsigned long long *h_result, uint32_t *h_err)
+{
+    CountStats *st = c.take<CountStats>(1);
+    unsigned long long *result = c.take<unsigned long long>(2);
+    uint32_t *next = c.take<uint32_t>(8);
+    uint32_t *small_list = c.take<uint32_t>((size_t)n + 1);
+    uint32_t *mid_list = c.take<uint32_t>((size_t)n + 1);
+    uint32_t *big_list = c.take<uint32_t>((size_t)n + 1);
+    uint32_t *hist = c.take<uint32_t>(kBitmapCap + 2);
+    uint32_t *cursor = c.take<uint32_t>(kBitmapCap + 2);
+    if (!c.ok) return cudaErrorMemoryAllocation;
+    // the rest of the workspace is list-path scratch
+    uint32_t *list_scratch = (uint32_t *)(c.base + c.used);
+    const size_t list_words = c.cap > c.used ? (c.cap - c.used) / sizeof(uint32_t) : 0;
+    (void)max_outdeg;
+
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(st, 0, sizeof(CountStats), s))) return e;
+    if ((e = cudaMemsetAsync(result, 0, 2 * sizeof(unsigned long long), s))) return e;
+    if ((e = cudaMemsetAsync(next, 0, 8 * sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(hist, 0, (kBitmapCap + 2) * sizeof(uint32_t), s))) return e;
+    const uint32_t need = k - 1;
+    const uint32_t blocks = (n + 255) / 256;
+    if (n) {
+        k_classify<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max,
+                                          small_list, big_list, hist, st, per_root);
+        k_mid_bins<<<1, 1024, 0, s>>>(hist, plan.bitmap_max + 1, cursor, st);
+        k_mid_scatter<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max,
+                                             cursor, mid_list);
+    }
+    CountStats hs;
+    if ((e = cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s))) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+#define CITRON_CASE(KK)                                                                          \
+    case KK:                                                                                     \
+        e = launch_count_k<KK>(n, dag_off, dag_cols, plan, hs, st, small_list, mid_list,         \
+                               big_list, next, list_scratch, list_words, result, per_root, err, \
+                               s, num_sms);                                                      \
+        break;
+    switch (k) {
+        CITRON_CASE(3)
+        CITRON_CASE(4)
+        CITRON_CASE(5)
+        CITRON_CASE(6)
+        CITRON_CASE(7)
+        CITRON_CASE(8)
+        CITRON_CASE(9)
+        CITRON_CASE(10)
+        CITRON_CASE(11)
+        CITRON_CASE(12)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CITRON_CASE
+    if (e) return e;
+    if ((e = cudaMemcpyAsync(h_result, result, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)))
+        return e;
+    if ((e = cudaMemcpyAsync(h_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t launch_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
+                                    unsigned long long *per_root, cudaStream_t s)
+{
+    if (n) k_per_root_trivial<<<(n + 255) / 256, 256, 0, s>>>(n, dag_off, k, per_root);
+    return cudaGetLastError();
+}
+
+}  // namespace citron_host

@@ -1,0 +1,73 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/citron.h
+declares; host-side argument checks answer without touching a GPU."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+HEADER = ROOT / "include" / "citron.h"
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(citron_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2112_10913_gb300 import build
+
+    return build.build()
+
+
+def test_header_lists_the_binding_exports():
+    import paper_2112_10913_gb300 as cg
+
+    assert declared_functions() == sorted(cg.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = ctypes.CDLL(str(built))
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(built):
+    import paper_2112_10913_gb300 as cg
+
+    L = cg.lib()
+    for code in range(7):
+        assert L.citron_status_str(code)
+    assert L.citron_version() >= 100
+
+
+def test_argument_checks_need_no_gpu(built):
+    import paper_2112_10913_gb300 as cg
+
+    L = cg.lib()
+    out = ctypes.c_uint64(0)
+    null = ctypes.c_void_p(0)
+    # k = 0 is invalid; k above the compiled maximum is unsupported; missing output is invalid
+    assert L.citron_count(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 0, 0, ctypes.byref(out), null, null, 0, null) == 1
+    assert L.citron_count(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 13, 0, ctypes.byref(out), null, null, 0, null) == 6
+    assert L.citron_count(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 3, 0, null, null, null, 0, null) == 1
+    # no workspace
+    assert L.citron_order(10, ctypes.c_void_p(1), ctypes.c_void_p(1), null, null, 0, null) == 2
+    # odd arc count cannot be a symmetric CSR
+    assert L.citron_build_dag(4, 3, ctypes.c_void_p(1), ctypes.c_void_p(1), null, ctypes.c_void_p(1),
+                              ctypes.c_void_p(1), null, null, 0, null) == 1
+    # n = 2^32 - 1 is reserved
+    assert L.citron_validate(0xFFFFFFFF, 0, ctypes.c_void_p(1), null, null, null, 0, null) == 1
+
+
+def test_workspace_size_grows_with_graph(built):
+    import paper_2112_10913_gb300 as cg
+
+    a = cg.citron_workspace_bytes(1000, 20000, 100)
+    b = cg.citron_workspace_bytes(100000, 2000000, 100)
+    assert 0 < a < b
+    # above the bitmap limit the sorted-list scratch is added
+    assert cg.citron_workspace_bytes(1000, 20000, 5000) > a

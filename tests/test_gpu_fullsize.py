@@ -1,0 +1,61 @@
+"""Parity at the full size of the R-MAT scale-20 workload (2^20 vertices, edge factor 16) in the
+launch configuration the bench times: DAG bytes against the oracle, the exact triangle count, and
+per-root counts for k = 4..6 on a seeded sample of roots the oracle can finish one by one."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2112_10913_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    return gg.config2_rmat()
+
+
+@pytest.fixture(scope="module")
+def dev(gpu, rmat20):
+    return gpu.DeviceGraph(rmat20, relabel=True)
+
+
+def test_dag_bytes_full(gpu, oracle_lib, rmat20, dev):
+    g = rmat20
+    rank = oracle_lib.degree_rank(g.off, g.n)
+    assert np.array_equal(dev.rank.cpu().numpy().view(np.uint32), rank)
+    off, cols = oracle_lib.dag_by_rank(g.off, g.cols, g.n, rank, relabel=True)
+    goff, gcols = dev.dag_numpy()
+    assert np.array_equal(goff, off) and np.array_equal(gcols, cols)
+    G0 = gpu.DeviceGraph(g, relabel=False)
+    off0, cols0 = oracle_lib.gen_ordering(g.off, g.cols, g.n)
+    goff0, gcols0 = G0.dag_numpy()
+    assert np.array_equal(goff0, off0) and np.array_equal(gcols0, cols0)
+
+
+def test_triangles_full(oracle_lib, dev):
+    off, cols = dev.dag_numpy()
+    assert dev.count(3) == oracle_lib.count(off, cols, dev.n, 3)
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_sampled_roots(oracle_lib, dev, k):
+    off, cols = dev.dag_numpy()
+    n = dev.n
+    pr = torch.zeros(n, dtype=torch.int64, device="cuda")
+    total = dev.count(k, per_root=pr)
+    got = pr.cpu().numpy().view(np.uint64)
+    assert int(got.sum(dtype=np.uint64)) == total
+    outdeg = np.diff(off).astype(np.int64)
+    # seeded sample: 2000 roots of the warp path, 1500 of the bitmap path (out-degree > 32)
+    light = np.nonzero((outdeg >= k - 1) & (outdeg <= 32))[0]
+    heavy = np.nonzero(outdeg > 32)[0]
+    pick = np.concatenate([light[gg.permutation(k, 1, light.size)[:2000]],
+                           heavy[gg.permutation(k, 2, heavy.size)[:1500]]])
+    # keep roots the oracle can finish quickly (bounded work), at most 3e9 cliques in all
+    pick = pick[got[pick] <= 5e7]
+    pick = pick[np.cumsum(got[pick].astype(np.float64)) <= 3e9]
+    assert pick.size > 1000
+    _, want = oracle_lib.count_roots(off, cols, n, k, pick.astype(np.uint32), per_root=True)
+    assert np.array_equal(got[pick], want)

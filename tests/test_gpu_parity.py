@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (called through the C ABI) with the oracle: bit-exact ranks, DAG CSR
+bytes and uint64 counts, on seeded inputs that span several tiles with ragged tails, on every
+counting path (warp-register, shared-memory bitmap, sorted list), and on the edge cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2112_10913_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+def dag_equal(G, off, cols):
+    goff, gcols = G.dag_numpy()
+    assert np.array_equal(goff, off), "DAG offsets differ"
+    assert np.array_equal(gcols, cols), "DAG columns differ"
+
+
+SMALL_GRAPHS = {
+    "fig1": gg.fig1,
+    "K33": lambda: gg.complete(33),
+    "T(40,6)": lambda: gg.turan(40, 6),
+    "CP(12)": lambda: gg.cocktail_party(12),
+    "er2000+K12": gg.config1_er_planted,
+    "rmat-n6000": lambda: gg.small_rmat(21, 6000, 24.0),
+    "er-n9000": lambda: gg.small_er(22, 9000, 18.0),
+    "rmat-n50000": lambda: gg.small_rmat(23, 50000, 30.0),
+}
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return {k: f() for k, f in SMALL_GRAPHS.items()}
+
+
+@pytest.mark.parametrize("name", list(SMALL_GRAPHS))
+def test_rank_is_degree_order(gpu, oracle_lib, graphs, name):
+    g = graphs[name]
+    G = gpu.DeviceGraph(g, relabel=True)
+    assert np.array_equal(G.rank.cpu().numpy().view(np.uint32), oracle_lib.degree_rank(g.off, g.n))
+
+
+@pytest.mark.parametrize("name", list(SMALL_GRAPHS))
+def test_gen_ordering_dag_bytes(gpu, oracle_lib, graphs, name):
+    g = graphs[name]
+    G = gpu.DeviceGraph(g, relabel=False)
+    off, cols = oracle_lib.gen_ordering(g.off, g.cols, g.n)
+    dag_equal(G, off, cols)
+    assert G.max_outdeg == int(np.diff(off).max())
+
+
+@pytest.mark.parametrize("name", list(SMALL_GRAPHS))
+def test_relabelled_dag_bytes(gpu, oracle_lib, graphs, name):
+    g = graphs[name]
+    G = gpu.DeviceGraph(g, relabel=True)
+    rank = oracle_lib.degree_rank(g.off, g.n)
+    off, cols = oracle_lib.dag_by_rank(g.off, g.cols, g.n, rank, relabel=True)
+    dag_equal(G, off, cols)
+    assert G.max_outdeg == int(np.diff(off).max())
+
+
+@pytest.mark.parametrize("which", ["random", "identity", "core"])
+def test_dag_of_any_rank(gpu, oracle_lib, graphs, which):
+    g = graphs["rmat-n6000"]
+    if which == "random":
+        rank = gg.permutation(5, 5, g.n).argsort().astype(np.uint32)
+    elif which == "identity":
+        rank = np.arange(g.n, dtype=np.uint32)
+    else:
+        rank = oracle_lib.core_rank(g.off, g.cols, g.n)
+    G = gpu.DeviceGraph(g, rank=rank)
+    off, cols = oracle_lib.dag_by_rank(g.off, g.cols, g.n, rank, relabel=True)
+    dag_equal(G, off, cols)
+    # the count does not depend on the ordering
+    ref = oracle_lib.count_graph(g, 4)
+    assert G.count(4) == ref
+
+
+PATHS = {
+    "default": {},
+    "bitmap-only": dict(small_max=1, bitmap_max=1024),
+    "small+list": dict(small_max=32, bitmap_max=32),
+    "list-only": dict(small_max=1, bitmap_max=1),
+    "narrow-cta": dict(warps_per_cta=2),
+}
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+@pytest.mark.parametrize("name", ["fig1", "K33", "T(40,6)", "CP(12)", "er2000+K12", "rmat-n6000", "er-n9000"])
+@pytest.mark.parametrize("relabel", [True, False])
+def test_counts_match_oracle(gpu, oracle_lib, graphs, path, name, relabel):
+    g = graphs[name]
+    G = gpu.DeviceGraph(g, relabel=relabel)
+    off, cols = G.dag_numpy()
+    for k in range(1, 8):
+        want = oracle_lib.count(off, cols, g.n, k)
+        assert G.count(k, **PATHS[path]) == want, (k, path)
+
+
+@pytest.mark.parametrize("path", ["default", "list-only"])
+def test_per_root_counts(gpu, oracle_lib, graphs, path):
+    g = graphs["rmat-n50000"]
+    G = gpu.DeviceGraph(g, relabel=True)
+    off, cols = G.dag_numpy()
+    roots = np.arange(g.n, dtype=np.uint32)
+    for k in (3, 4, 5):
+        pr = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+        tot = G.count(k, per_root=pr, **PATHS[path])
+        want_tot, want = oracle_lib.count_roots(off, cols, g.n, k, roots, per_root=True)
+        got = pr.cpu().numpy().view(np.uint64)
+        assert tot == want_tot
+        assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+
+
+def test_closed_forms(gpu):
+    for n in (1, 2, 5, 32, 33, 64, 200):
+        G = gpu.DeviceGraph(gg.complete(n))
+        for k in range(1, min(n + 2, 11)):
+            assert G.count(k) == math.comb(n, k), (n, k)
+    G = gpu.DeviceGraph(gg.cocktail_party(14))
+    for k in range(1, 13):
+        assert G.count(k) == math.comb(14, k) * 2 ** k
+    parts = [9, 7, 7, 5, 3, 1]
+    G = gpu.DeviceGraph(gg.complete_multipartite(parts))
+    for k in range(1, 8):
+        coef = [1]
+        for s in parts:
+            coef = [a + s * b for a, b in zip(coef + [0], [0] + coef)]
+        assert G.count(k) == (coef[k] if k < len(coef) else 0)
+
+
+def test_list_path_beyond_bitmap_capacity(gpu):
+    # K_1100: out-degrees 0..1099 under any ordering; roots above 1024 take the sorted-list path
+    G = gpu.DeviceGraph(gg.complete(1100))
+    assert G.max_outdeg == 1099
+    assert G.count(3) == math.comb(1100, 3)
+
+
+def test_triangles_trace_config1(gpu):
+    import scipy.sparse as sp
+
+    g = gg.config1_er_planted()
+    rows = np.repeat(np.arange(g.n), np.diff(g.off).astype(np.int64))
+    a = sp.csr_matrix((np.ones(g.cols.size), (rows, g.cols.astype(np.int64))), shape=(g.n, g.n))
+    assert gpu.DeviceGraph(g).count(3) == int(round((a @ a).multiply(a).sum() / 6))
+
+
+def test_edge_cases(gpu, oracle_lib):
+    # isolated vertices only
+    g = gg.csr_from_edges(10, [], [])
+    G = gpu.DeviceGraph(g)
+    assert [G.count(k) for k in (1, 2, 3, 4)] == [10, 0, 0, 0]
+    # one edge among many isolated vertices, ragged sizes
+    g = gg.csr_from_edges(4099, [7], [4000])
+    for relabel in (True, False):
+        G = gpu.DeviceGraph(g, relabel=relabel)
+        assert [G.count(k) for k in (1, 2, 3)] == [4099, 1, 0]
+    # k above max out-degree + 1 is zero; k = 12 (largest supported) on K_14
+    G = gpu.DeviceGraph(gg.complete(14))
+    assert G.count(12) == math.comb(14, 12)
+    g = gg.small_rmat(30, 3000, 10.0)
+    G = gpu.DeviceGraph(g)
+    assert G.count(G.max_outdeg + 2) == 0
+
+
+def test_invalid_arguments(gpu):
+    G = gpu.DeviceGraph(gg.fig1())
+    with pytest.raises(gpu.CitronError) as e:
+        G.count(0)
+    assert e.value.name == "CITRON_E_INVALID"
+    for k in (13, 15):
+        with pytest.raises(gpu.CitronError) as e:
+            G.count(k)
+        assert e.value.name == "CITRON_E_UNSUPPORTED"
+
+
+def test_validate_on_device(gpu, oracle_lib):
+    g = gg.fig1()
+    ws = gpu.alloc_workspace(g.n, g.cols.size)
+
+    def run(cols):
+        off_t = torch.from_numpy(g.off.view(np.int64)).cuda()
+        cols_t = torch.from_numpy(cols.view(np.int32)).cuda()
+        return gpu.citron_validate(g.n, off_t, cols_t, ws)
+
+    assert run(g.cols.copy()) == 0
+    for pos, val, want in [(0, 0, 4), (2, 6, 5), (2, 9, 2)]:
+        bad = g.cols.copy()
+        bad[pos] = val
+        assert run(bad) == oracle_lib.validate(g.off, bad, g.n) == want
+    bad = g.cols.copy()
+    bad[0], bad[1] = bad[1], bad[0]
+    assert run(bad) == 3
+
+
+def test_host_pipeline(gpu, oracle_lib, graphs):
+    g = graphs["rmat-n50000"]
+    buf = torch.empty(gpu.citron_host_buffer_bytes(g.n, g.cols.size), dtype=torch.uint8, device="cuda")
+    ws = gpu.alloc_workspace(g.n, g.cols.size, 2048)
+    ks = [1, 2, 3, 4, 5, 6]
+    got = gpu.citron_count_host(g.n, g.off, g.cols, ks, buf, ws)
+    assert got == [oracle_lib.count_graph(g, k) for k in ks]
