@@ -118,19 +118,32 @@ citron_status citron_count(uint32_t n, const uint64_t *d_dag_off, const uint32_t
                            uint64_t *d_per_root, void *ws, size_t ws_bytes, void *stream);
 
 /*
- * citron_count_tuned -- citron_count with the internal path thresholds exposed (for tests that
- * must reach every path on small graphs and for the autotuner):
- *   small_max: roots with out-degree <= small_max use the warp-register path (0..32);
- *   bitmap_max: roots with out-degree <= bitmap_max use the shared-memory bitmap path
- *               (small_max < bitmap_max <= 1024); larger roots use the sorted-list path.
- *   warps_per_cta: warps of the bitmap-path blocks (1..16).
- * Any argument 0 selects the default.  Same results as citron_count.
+ * citron_count_ex -- citron_count with options: the internal path thresholds (for tests that must
+ * reach every path on small graphs, and for tuning), device timing of the counting kernels, and
+ * a count of the word operations the bitmap path performs (for roofline accounting).
+ *   opts (host, required): see citron_count_opts; its "in" fields are read, its "out" fields
+ *   written.  Same count as citron_count.  Synchronises `stream`.
  */
-citron_status citron_count_tuned(uint32_t n, const uint64_t *d_dag_off,
-                                 const uint32_t *d_dag_cols, uint32_t k, uint32_t max_outdeg,
-                                 uint32_t small_max, uint32_t bitmap_max, uint32_t warps_per_cta,
-                                 uint64_t *h_count, uint64_t *d_per_root, void *ws,
-                                 size_t ws_bytes, void *stream);
+#define CITRON_COUNT_TIME_KERNELS 1u /* fill kernel_ms (events on `stream`) */
+#define CITRON_COUNT_WORK 2u         /* fill work_ops (a separately compiled, instrumented kernel) */
+typedef struct {
+    uint32_t small_max;      /* in: warp-register path for out-degree <= small_max, 0..32 (0: 32) */
+    uint32_t bitmap_max;     /* in: shared-memory bitmap path up to this out-degree, <= 1024
+                                (0: 1024); larger roots take the sorted-list path */
+    uint32_t warps_per_cta;  /* in: warps per bitmap-path block, 1..32 (0: 32); fewer are used
+                                when the block's shared memory would not fit */
+    uint32_t flags;          /* in: CITRON_COUNT_* bits */
+    uint64_t *d_per_root;    /* in: optional device array of n uint64, as in citron_count */
+    uint64_t work_ops;       /* out: 32-bit AND+POPC word operations of the bitmap path */
+    float kernel_ms[3];      /* out: device ms of the warp-register, bitmap, sorted-list kernels */
+} citron_count_opts;
+
+citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
+                              uint32_t k, uint32_t max_outdeg, citron_count_opts *opts,
+                              uint64_t *h_count, void *ws, size_t ws_bytes, void *stream);
+
+/* Number of CUDA kernels this library has launched since it was loaded (all threads). */
+uint64_t citron_kernel_launches(void);
 
 /*
  * citron_count_host -- the whole hot path from HOST buffers: copies the CSR (h_off[n+1],

@@ -35,10 +35,28 @@ EXPORTS = (
     "citron_order",
     "citron_build_dag",
     "citron_count",
-    "citron_count_tuned",
+    "citron_count_ex",
+    "citron_kernel_launches",
     "citron_host_buffer_bytes",
     "citron_count_host",
 )
+
+COUNT_TIME_KERNELS = 1
+COUNT_WORK = 2
+
+
+class CountOpts(ctypes.Structure):
+    """Mirror of citron_count_opts (include/citron.h)."""
+
+    _fields_ = [
+        ("small_max", ctypes.c_uint32),
+        ("bitmap_max", ctypes.c_uint32),
+        ("warps_per_cta", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("d_per_root", ctypes.c_void_p),
+        ("work_ops", ctypes.c_uint64),
+        ("kernel_ms", ctypes.c_float * 3),
+    ]
 
 
 class CitronError(RuntimeError):
@@ -75,8 +93,10 @@ def lib() -> ctypes.CDLL:
     L.citron_build_dag.restype = i32
     L.citron_count.argtypes = [u32, vp, vp, u32, u32, vp, vp, vp, sz, vp]
     L.citron_count.restype = i32
-    L.citron_count_tuned.argtypes = [u32, vp, vp, u32, u32, u32, u32, u32, vp, vp, vp, sz, vp]
-    L.citron_count_tuned.restype = i32
+    L.citron_count_ex.argtypes = [u32, vp, vp, u32, u32, vp, vp, vp, sz, vp]
+    L.citron_count_ex.restype = i32
+    L.citron_kernel_launches.argtypes = []
+    L.citron_kernel_launches.restype = u64
     L.citron_host_buffer_bytes.argtypes = [u32, u64]
     L.citron_host_buffer_bytes.restype = sz
     L.citron_count_host.argtypes = [u32, u64, vp, vp, vp, u32, vp, vp, sz, vp, sz, vp]
@@ -154,18 +174,30 @@ def citron_build_dag(n: int, off, cols, rank, dag_off, dag_cols, ws, stream=None
 
 
 def citron_count(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, per_root=None,
-                 stream=None, small_max: int = 0, bitmap_max: int = 0, warps_per_cta: int = 0) -> int:
+                 stream=None) -> int:
     out = ctypes.c_uint64(0)
-    if small_max or bitmap_max or warps_per_cta:
-        code = lib().citron_count_tuned(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg,
-                                        small_max, bitmap_max, warps_per_cta, ctypes.byref(out),
-                                        _dptr(per_root), _dptr(ws), _nbytes(ws), _stream(stream))
-    else:
-        code = lib().citron_count(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg,
-                                  ctypes.byref(out), _dptr(per_root), _dptr(ws), _nbytes(ws),
-                                  _stream(stream))
-    _check(code, f"citron_count(k={k})")
+    _check(lib().citron_count(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg, ctypes.byref(out),
+                              _dptr(per_root), _dptr(ws), _nbytes(ws), _stream(stream)),
+           f"citron_count(k={k})")
     return int(out.value)
+
+
+def citron_count_ex(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, per_root=None,
+                    stream=None, small_max: int = 0, bitmap_max: int = 0, warps_per_cta: int = 0,
+                    time_kernels: bool = False, count_work: bool = False):
+    """Returns (count, CountOpts) -- the options carry work_ops and kernel_ms on return."""
+    o = CountOpts(small_max, bitmap_max, warps_per_cta,
+                  (COUNT_TIME_KERNELS if time_kernels else 0) | (COUNT_WORK if count_work else 0),
+                  _dptr(per_root).value, 0)
+    out = ctypes.c_uint64(0)
+    _check(lib().citron_count_ex(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg, ctypes.byref(o),
+                                 ctypes.byref(out), _dptr(ws), _nbytes(ws), _stream(stream)),
+           f"citron_count_ex(k={k})")
+    return int(out.value), o
+
+
+def citron_kernel_launches() -> int:
+    return int(lib().citron_kernel_launches())
 
 
 def citron_host_buffer_bytes(n: int, arcs: int) -> int:
@@ -226,8 +258,11 @@ class DeviceGraph:
             self.ws = alloc_workspace(self.n, self.arcs, self.max_outdeg, device=dev)
 
     def count(self, k: int, per_root=None, stream=None, **tuned) -> int:
+        if tuned:
+            return citron_count_ex(self.n, self.dag_off, self.dag_cols, k, self.ws, self.max_outdeg,
+                                   per_root, stream, **tuned)[0]
         return citron_count(self.n, self.dag_off, self.dag_cols, k, self.ws, self.max_outdeg,
-                            per_root, stream, **tuned)
+                            per_root, stream)
 
     def dag_numpy(self):
         off = self.dag_off.cpu().numpy().view(np.uint64)

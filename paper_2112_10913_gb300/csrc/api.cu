@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "citron.h"
 #include "common.cuh"
 
@@ -19,9 +21,12 @@ cudaError_t launch_validate(uint32_t n, uint64_t arcs, const uint64_t *off, cons
                             uint32_t *bad, cudaStream_t st, int num_sms);
 size_t count_ws_bytes(uint32_t n, uint32_t max_outdeg, int num_sms);
 cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
-                      uint32_t max_outdeg, const CountPlan &plan, unsigned long long *per_root,
-                      uint32_t *err, Carver &c, cudaStream_t s, int num_sms,
-                      unsigned long long *h_result, uint32_t *h_err);
+                      CountRun &run, uint32_t *err, Carver &c, cudaStream_t s, int num_sms,
+                      unsigned long long *h_result);
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 cudaError_t launch_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
                                     unsigned long long *per_root, cudaStream_t s);
 }  // namespace citron_host
@@ -180,23 +185,27 @@ citron_status citron_build_dag(uint32_t n, uint64_t arcs, const uint64_t *d_off,
     return finish_sync(ws, s, CITRON_OK);
 }
 
-citron_status citron_count_tuned(uint32_t n, const uint64_t *d_dag_off,
-                                 const uint32_t *d_dag_cols, uint32_t k, uint32_t max_outdeg,
-                                 uint32_t small_max, uint32_t bitmap_max, uint32_t warps_per_cta,
-                                 uint64_t *h_count, uint64_t *d_per_root, void *ws,
-                                 size_t ws_bytes, void *stream)
+citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
+                              uint32_t k, uint32_t max_outdeg, citron_count_opts *opts,
+                              uint64_t *h_count, void *ws, size_t ws_bytes, void *stream)
 {
-    if (!h_count || !d_dag_off || n == 0xffffffffu || k == 0) return CITRON_E_INVALID;
+    (void)max_outdeg;  // the count derives every size it needs from the DAG itself
+    if (!h_count || !opts || !d_dag_off || n == 0xffffffffu || k == 0) return CITRON_E_INVALID;
     if (k > CITRON_MAX_K) return CITRON_E_UNSUPPORTED;
-    if (small_max > 32 || bitmap_max > 1024 || warps_per_cta > 16) return CITRON_E_INVALID;
-    CountPlan plan;
-    if (small_max) plan.small_max = small_max;
-    if (bitmap_max) plan.bitmap_max = bitmap_max;
-    if (warps_per_cta) plan.warps_per_cta = warps_per_cta;
-    if (plan.bitmap_max < plan.small_max) plan.bitmap_max = plan.small_max;
+    if (opts->small_max > 32 || opts->bitmap_max > 1024 || opts->warps_per_cta > 32)
+        return CITRON_E_INVALID;
+    CountRun run;
+    if (opts->small_max) run.plan.small_max = opts->small_max;
+    if (opts->bitmap_max) run.plan.bitmap_max = opts->bitmap_max;
+    if (opts->warps_per_cta) run.plan.warps_per_cta = opts->warps_per_cta;
+    if (run.plan.bitmap_max < run.plan.small_max) run.plan.bitmap_max = run.plan.small_max;
+    run.per_root = (unsigned long long *)opts->d_per_root;
+    run.time_kernels = (opts->flags & CITRON_COUNT_TIME_KERNELS) != 0;
+    run.count_work = (opts->flags & CITRON_COUNT_WORK) != 0;
+    opts->work_ops = 0;
+    opts->kernel_ms[0] = opts->kernel_ms[1] = opts->kernel_ms[2] = 0.f;
     cudaStream_t s = (cudaStream_t)stream;
     if (!ws_ok(ws, ws_bytes, kHeader)) return CITRON_E_WORKSPACE;
-    unsigned long long *per_root = (unsigned long long *)d_per_root;
     if (k <= 2) {
         cudaError_t e = cudaSuccess;
         if (k == 1) {
@@ -207,19 +216,20 @@ citron_status citron_count_tuned(uint32_t n, const uint64_t *d_dag_off,
             if (!e) e = cudaStreamSynchronize(s);
             *h_count = m;
         }
-        if (!e && per_root) e = launch_per_root_trivial(n, d_dag_off, k, per_root, s);
+        if (!e && run.per_root) e = launch_per_root_trivial(n, d_dag_off, k, run.per_root, s);
         if (e) return from_cuda(e);
         return finish_sync(ws, s, CITRON_OK);
     }
     if (n && !d_dag_cols) return CITRON_E_INVALID;
     Carver c((char *)ws + kHeader, ws_bytes - kHeader);
     unsigned long long result = 0;
-    uint32_t dev_err = 0;
-    cudaError_t e = run_count(n, d_dag_off, d_dag_cols, k, max_outdeg, plan, per_root,
-                              err_word(ws), c, s, sm_count(), &result, &dev_err);
+    cudaError_t e = run_count(n, d_dag_off, d_dag_cols, k, run, err_word(ws), c, s, sm_count(),
+                              &result);
     if (e) return from_cuda(e);
     citron_status st = finish_sync(ws, s, CITRON_OK);
     if (st == CITRON_OK) *h_count = result;
+    opts->work_ops = run.work;
+    for (int i = 0; i < 3; i++) opts->kernel_ms[i] = run.kernel_ms[i];
     return st;
 }
 
@@ -227,9 +237,13 @@ citron_status citron_count(uint32_t n, const uint64_t *d_dag_off, const uint32_t
                            uint32_t k, uint32_t max_outdeg, uint64_t *h_count,
                            uint64_t *d_per_root, void *ws, size_t ws_bytes, void *stream)
 {
-    return citron_count_tuned(n, d_dag_off, d_dag_cols, k, max_outdeg, 0, 0, 0, h_count,
-                              d_per_root, ws, ws_bytes, stream);
+    citron_count_opts o = {};
+    o.d_per_root = d_per_root;
+    return citron_count_ex(n, d_dag_off, d_dag_cols, k, max_outdeg, &o, h_count, ws, ws_bytes,
+                           stream);
 }
+
+uint64_t citron_kernel_launches(void) { return launches(); }
 
 size_t citron_host_buffer_bytes(uint32_t n, uint64_t arcs)
 {

@@ -170,8 +170,22 @@ namespace citron_host {
 struct CountPlan {
     uint32_t small_max = 32;       // roots with out-degree <= this use the warp-register path
     uint32_t bitmap_max = 1024;    // ... <= this use the shared-memory bitmap path
-    uint32_t warps_per_cta = 16;   // warps per block of the bitmap path
+    uint32_t warps_per_cta = 32;   // warps per block of the bitmap path (fewer if shared memory is short)
 };
+
+// Options and outputs of one counting call.
+struct CountRun {
+    CountPlan plan;
+    unsigned long long *per_root = nullptr;  // device, optional
+    bool count_work = false;                 // instrumented launch: count word operations
+    bool time_kernels = false;               // record device time of the counting kernels
+    unsigned long long work = 0;             // out: word operations (AND + POPC of 32-bit words)
+    float kernel_ms[3] = {0, 0, 0};          // out: warp-register, bitmap, sorted-list kernels
+};
+
+// Number of kernels this library has launched (all devices, all threads).
+void note_launches(unsigned n);
+unsigned long long launches();
 
 struct Carver {
     char *base;

@@ -220,33 +220,141 @@ __global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
 // ------------------------------------------------------------------------------------------
 // Shared-memory bitmap path (small_max < D <= 1024).
 
-// Lane l holds word l of the candidate set (words >= W are zero).  Adds lane-partial counts of
-// the R-cliques inside the candidate set to acc.
-template <int R>
-__device__ __forceinline__ void warp_dfs(const uint32_t *rows, uint32_t RS, uint32_t W, uint32_t c,
-                                         int lane, unsigned long long &acc)
+// Per-warp view of the block's local subgraph and the warp's private scratch.
+//   rows : D x RS words, row i = bits j with L[j] in N+(L[i]) (RS odd: column reads by
+//          different rows fall in different banks)
+//   tri  : every row only has bits above its own index (true for a DAG relabelled to ranks, whose
+//          rows are sorted in the DAG order); lets the loops skip the words below an element.
+//   elem : the current candidate set as a list of indices (compaction buffer)
+//   cbuf : the current candidate set's words
+//   lbuf : one candidate set per lane, word-major ([w * 32 + lane]), so that lanes reading
+//          their own word w always hit 32 different banks
+struct WarpCtx {
+    const uint32_t *rows;
+    uint32_t RS, W;
+    bool tri;
+    uint16_t *elem;
+    uint32_t *cbuf;
+    uint32_t *lbuf;
+};
+
+// Number of DAG arcs inside the lane's own candidate set lb (words [lo, hi)): the penultimate
+// level of Counting, which only adds subgraph degrees.  WORK adds the 32-bit word operations
+// (AND + POPC) performed to `work`.
+template <bool WORK>
+__device__ __forceinline__ uint32_t lane_arcs(const WarpCtx &x, const uint32_t *lb, int lo, int hi,
+                                              unsigned long long &work)
+{
+    uint32_t s = 0;
+    for (int w = lo; w < hi; w++) {
+        uint32_t y = lb[w * 32];
+        if (WORK) work += (unsigned long long)__popc(y) * (uint32_t)(hi - (x.tri ? w : lo));
+        while (y) {
+            const uint32_t b = (uint32_t)(w << 5) + __ffs(y) - 1;
+            y &= y - 1;
+            const uint32_t *rb = x.rows + b * x.RS;
+            int w2 = x.tri ? w : lo;
+            // two independent word pairs per step keep two shared-memory loads in flight
+            for (; w2 + 1 < hi; w2 += 2)
+                s += __popc(lb[w2 * 32] & rb[w2]) + __popc(lb[w2 * 32 + 32] & rb[w2 + 1]);
+            if (w2 < hi) s += __popc(lb[w2 * 32] & rb[w2]);
+        }
+    }
+    return s;
+}
+
+// Writes the candidate set (lane word c) to cbuf and its member indices to elem; returns the
+// member count and the range [clo, chi) of its non-zero words.
+__device__ __forceinline__ uint32_t compact(const WarpCtx &x, uint32_t c, int lane, int &clo, int &chi)
+{
+    const uint32_t pc = __popc(c);
+    const uint32_t incl = warp_incl_scan(pc);
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    uint32_t pos = incl - pc;
+    if (lane < (int)x.W) x.cbuf[lane] = c;
+    uint32_t y = c;
+    while (y) {
+        x.elem[pos++] = (uint16_t)((lane << 5) + __ffs(y) - 1);
+        y &= y - 1;
+    }
+    const uint32_t nz = __ballot_sync(kFull, c != 0);
+    clo = nz ? __ffs(nz) - 1 : 0;
+    chi = nz ? 32 - __clz(nz) : 0;
+    __syncwarp();
+    return total;
+}
+
+// Counts the R-cliques inside the candidate set whose word w sits in lane w (words >= W are
+// zero); adds lane-partial sums to acc.
+//   R >= 4: warp-uniform walk over the members a; the next candidate set c ∧ row_a is again
+//           spread over the lanes (one shared-memory load per lane).
+//   R == 3: members are compacted and dealt to lanes; each lane builds its own c ∧ row_a and
+//           sums its arcs (the last two levels run lane-parallel).
+//   R == 2: members dealt to lanes, each adds |c ∧ row_a|.
+template <int R, bool WORK>
+__device__ __forceinline__ void warp_dfs(const WarpCtx &x, uint32_t c, int lane,
+                                         unsigned long long &acc, unsigned long long &work)
 {
     if constexpr (R == 1) {
         acc += __popc(c);
     } else if constexpr (R == 2) {
-        const uint32_t nzw = __ballot_sync(kFull, c != 0);
-        uint32_t outer = nzw;
-        uint32_t s = 0;
-        while (outer) {
-            const int w = __ffs(outer) - 1;
-            outer &= outer - 1;
-            const uint32_t cw = __shfl_sync(kFull, c, w);
-            const bool act = (cw >> lane) & 1;
-            const uint32_t *row = rows + (size_t)(w * 32 + lane) * RS;
-            uint32_t inner = nzw;
-            while (inner) {
-                const int w2 = __ffs(inner) - 1;
-                inner &= inner - 1;
-                const uint32_t v = __shfl_sync(kFull, c, w2);
-                if (act) s += __popc(v & row[w2]);
+        const uint32_t nz = __ballot_sync(kFull, c != 0);
+        if (__popc(nz) <= 4) {
+            // few words: lane l takes bit l of each non-zero word in turn
+            if (lane < (int)x.W) x.cbuf[lane] = c;
+            __syncwarp();
+            const int chi = 32 - __clz(nz);
+            uint32_t outer = nz, s = 0;
+            while (outer) {
+                const int w = __ffs(outer) - 1;
+                outer &= outer - 1;
+                const uint32_t cw = x.cbuf[w];
+                if ((cw >> lane) & 1) {
+                    const uint32_t *ra = x.rows + (uint32_t)(w * 32 + lane) * x.RS;
+                    const int w0 = x.tri ? w : (__ffs(nz) - 1);
+                    if (WORK) work += (uint32_t)(chi - w0);
+                    for (int w2 = w0; w2 < chi; w2++) s += __popc(x.cbuf[w2] & ra[w2]);
+                }
             }
+            acc += s;
+            __syncwarp();
+        } else {
+            int clo, chi;
+            const uint32_t total = compact(x, c, lane, clo, chi);
+            uint32_t s = 0;
+            for (uint32_t i = lane; i < total; i += 32) {
+                const uint32_t a = x.elem[i];
+                const uint32_t *ra = x.rows + a * x.RS;
+                const int w0 = x.tri ? (int)(a >> 5) : clo;
+                if (WORK) work += (uint32_t)(chi - w0);
+                for (int w = w0; w < chi; w++) s += __popc(x.cbuf[w] & ra[w]);
+            }
+            acc += s;
+            __syncwarp();
         }
-        acc += s;
+    } else if constexpr (R == 3) {
+        int clo, chi;
+        const uint32_t total = compact(x, c, lane, clo, chi);
+        uint32_t *lb = x.lbuf + lane;
+        for (uint32_t i = lane; i < total; i += 32) {
+            const uint32_t a = x.elem[i];
+            const uint32_t *ra = x.rows + a * x.RS;
+            uint32_t cnt = 0;
+            int nlo = 32, nhi = 0;
+            const int w0 = x.tri ? (int)(a >> 5) : clo;
+            if (WORK) work += (uint32_t)(chi - w0);
+            for (int w = w0; w < chi; w++) {
+                const uint32_t v = x.cbuf[w] & ra[w];
+                lb[w * 32] = v;
+                if (v) {
+                    cnt += __popc(v);
+                    nlo = min(nlo, w);
+                    nhi = w + 1;
+                }
+            }
+            if (cnt >= 2) acc += lane_arcs<WORK>(x, lb, nlo, nhi, work);
+        }
+        __syncwarp();
     } else {
         uint32_t rem = c;
         for (;;) {
@@ -256,34 +364,49 @@ __device__ __forceinline__ void warp_dfs(const uint32_t *rows, uint32_t RS, uint
             const uint32_t word = __shfl_sync(kFull, rem, wl);
             const uint32_t a = wl * 32 + __ffs(word) - 1;
             if (lane == wl) rem &= rem - 1;
-            const uint32_t c2 = lane < W ? (c & rows[a * RS + lane]) : 0u;
+            const uint32_t c2 = lane < (int)x.W ? (c & x.rows[a * x.RS + lane]) : 0u;
+            if (WORK && lane < (int)x.W) work += 1;
             const uint32_t cnt = __reduce_add_sync(kFull, __popc(c2));
-            if (cnt >= R - 1) warp_dfs<R - 1>(rows, RS, W, c2, lane, acc);
+            if (cnt >= R - 1) warp_dfs<R - 1, WORK>(x, c2, lane, acc, work);
         }
     }
 }
 
-constexpr int kMidMaxWarps = 16;
+// Shared-memory words one warp needs for roots of out-degree <= dcap (dcap multiple of 32).
+__host__ __device__ __forceinline__ uint32_t warp_scratch_words(uint32_t dcap)
+{
+    return dcap / 2 + 32 + 32 * (dcap / 32);
+}
 
-template <int K>
-__global__ __launch_bounds__(kMidMaxWarps * 32) void k_count_mid(const uint64_t *__restrict__ dag_off,
-                            const uint32_t *__restrict__ dag_cols, const uint32_t *__restrict__ list,
-                            const CountStats *st, uint32_t *next, uint32_t dcap,
-                            unsigned long long *result, unsigned long long *per_root,
-                            uint32_t *err)
+constexpr int kMidMaxWarps = 32;
+
+template <int K, bool WORK>
+__global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
+    const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
+    const uint32_t *__restrict__ list, const CountStats *st, uint32_t *next, uint32_t dcap,
+    unsigned long long *result, unsigned long long *per_root, unsigned long long *work_out,
+    uint32_t *err)
 {
     extern __shared__ uint32_t smem[];
+    const uint32_t rs_cap = (dcap / 32) | 1;
     uint32_t *sL = smem;
     uint32_t *rows = smem + dcap;
-    __shared__ uint32_t s_idx, s_task;
+    __shared__ uint32_t s_idx, s_task, s_tri;
     __shared__ unsigned long long s_acc[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t *wscr = rows + (size_t)dcap * rs_cap + (size_t)w * warp_scratch_words(dcap);
+    WarpCtx x;
+    x.rows = rows;
+    x.elem = reinterpret_cast<uint16_t *>(wscr);
+    x.cbuf = wscr + dcap / 2;
+    x.lbuf = wscr + dcap / 2 + 32;
     const uint32_t nlist = st->n_mid;
     unsigned long long block_total = 0;  // meaningful in thread 0
     for (;;) {
         if (threadIdx.x == 0) {
             s_idx = atomicAdd(next, 1u);
             s_task = 0;
+            s_tri = 1;
         }
         __syncthreads();
         const uint32_t idx = s_idx;
@@ -297,25 +420,40 @@ __global__ __launch_bounds__(kMidMaxWarps * 32) void k_count_mid(const uint64_t 
             for (uint32_t i = threadIdx.x; i < D * RS; i += blockDim.x) rows[i] = 0;
         __syncthreads();
         const uint32_t lmax = sL[D - 1];
-        unsigned long long acc = 0;
-        // Build the local subgraph: row i = V(g_u) ∩ N+(a_i) (CITRON's GenSubgraph).
+        unsigned long long acc = 0, work = 0;
+        // Build the local subgraph: row i = V(g_u) ∩ N+(a_i) (CITRON's GenSubgraph).  Each step
+        // loads 64 entries of N+(a_i) (two per lane) so that two loads are in flight.
+        bool tri = true;
         for (uint32_t i = w; i < D; i += nw) {
             const uint32_t a = sL[i];
             const uint64_t b = dag_off[a], e = dag_off[a + 1];
-            for (uint64_t p = b; p < e; p += 32) {
-                const uint32_t y = p + lane < e ? dag_cols[p + lane] : 0xffffffffu;
-                if (__shfl_sync(kFull, y, 0) > lmax) break;
-                if (y <= lmax) {
-                    const uint32_t j = lower_bound_smem(sL, D, y);
-                    if (sL[j] == y) {
-                        if (K == 3) acc += 1;
-                        else atomicOr(&rows[i * RS + (j >> 5)], 1u << (j & 31));
+            for (uint64_t p = b; p < e; p += 64) {
+                const uint32_t y0 = p + lane < e ? dag_cols[p + lane] : 0xffffffffu;
+                const uint32_t y1 = p + 32 + lane < e ? dag_cols[p + 32 + lane] : 0xffffffffu;
+                if (__shfl_sync(kFull, y0, 0) > lmax) break;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t y = h ? y1 : y0;
+                    if (y <= lmax) {
+                        const uint32_t j = lower_bound_smem(sL, D, y);
+                        if (sL[j] == y) {
+                            if (K == 3) {
+                                acc += 1;
+                            } else {
+                                atomicOr(&rows[i * RS + (j >> 5)], 1u << (j & 31));
+                                tri &= j > i;
+                            }
+                        }
                     }
                 }
             }
         }
         if (K > 3) {
+            if (!__all_sync(kFull, tri) && lane == 0) s_tri = 0;
             __syncthreads();
+            x.RS = RS;
+            x.W = W;
+            x.tri = s_tri != 0;
             // Edge tasks (u, a_t): count (K-2)-cliques in row t.
             for (;;) {
                 uint32_t t = 0;
@@ -324,8 +462,12 @@ __global__ __launch_bounds__(kMidMaxWarps * 32) void k_count_mid(const uint64_t 
                 if (t >= D) break;
                 const uint32_t c = lane < W ? rows[t * RS + lane] : 0u;
                 const uint32_t cnt = __reduce_add_sync(kFull, __popc(c));
-                if (cnt >= K - 2) warp_dfs<K - 2>(rows, RS, W, c, lane, acc);
+                if (cnt >= K - 2) warp_dfs<K - 2, WORK>(x, c, lane, acc, work);
             }
+        }
+        if (WORK) {
+            const unsigned long long wsum = warp_sum_u64(work, err);
+            if (lane == 0 && wsum) atomicAdd(work_out, wsum);
         }
         const unsigned long long ws = warp_sum_u64(acc, err);
         if (lane == 0) s_acc[w] = ws;
@@ -334,15 +476,15 @@ __global__ __launch_bounds__(kMidMaxWarps * 32) void k_count_mid(const uint64_t 
             unsigned long long r = 0;
             bool wrapped = false;
             for (int i = 0; i < nw; i++) {
-                const unsigned long long s = r + s_acc[i];
-                wrapped |= s < r;
-                r = s;
+                const unsigned long long s2 = r + s_acc[i];
+                wrapped |= s2 < r;
+                r = s2;
             }
             if (wrapped) set_error(err, kDevOverflow);
             if (per_root) per_root[u] = r;
-            const unsigned long long s = block_total + r;
-            if (s < block_total) set_error(err, kDevOverflow);
-            block_total = s;
+            const unsigned long long s2 = block_total + r;
+            if (s2 < block_total) set_error(err, kDevOverflow);
+            block_total = s2;
         }
         __syncthreads();
     }
@@ -459,48 +601,110 @@ size_t count_ws_bytes(uint32_t n, uint32_t max_outdeg, int num_sms)
     s.take<uint32_t>((size_t)n + 1);          // big list
     s.take<uint32_t>(kBitmapCap + 2);         // mid histogram
     s.take<uint32_t>(kBitmapCap + 2);         // mid cursors
+    // sorted-list scratch: one (k-3)-level stack per warp, sized for the largest root, so that
+    // every root can take the list path (tuned thresholds send any root there)
     const uint32_t list_warps = (uint32_t)num_sms * kListWarps;
-    const size_t stride = max_outdeg > kBitmapCap ? max_outdeg : 0;
-    s.take<uint32_t>(stride * list_warps * (kMaxK - 3) + 1);
+    s.take<uint32_t>((size_t)max_outdeg * list_warps * (kMaxK - 3) + 1);
     return s.used;
 }
 
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool on;
+    cudaStream_t s;
+    Timer(bool enable, cudaStream_t st) : on(enable), s(st)
+    {
+        if (on && (cudaEventCreate(&a) || cudaEventCreate(&b))) on = false;
+        if (on) cudaEventRecord(a, s);
+    }
+    void stop() { if (on) cudaEventRecord(b, s); }
+    float ms()
+    {
+        float t = 0;
+        if (on && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&t, a, b);
+        return t;
+    }
+    ~Timer()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+template <int K, bool WORK>
+static cudaError_t launch_mid(uint32_t grid_cap, uint32_t dcap, uint32_t warps, size_t smem,
+                              const uint64_t *dag_off, const uint32_t *dag_cols,
+                              const uint32_t *mid_list, const CountStats *st, uint32_t *next,
+                              unsigned long long *result, unsigned long long *per_root,
+                              unsigned long long *work, uint32_t *err, cudaStream_t s, int num_sms)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_count_mid<K, WORK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_mid<K, WORK>, warps * 32,
+                                                           smem)))
+        return e;
+    if (per_sm < 1) per_sm = 1;
+    uint32_t grid = (uint32_t)(num_sms * per_sm);
+    if (grid > grid_cap) grid = grid_cap;
+    k_count_mid<K, WORK><<<grid, warps * 32, smem, s>>>(dag_off, dag_cols, mid_list, st, next, dcap,
+                                                        result, per_root, work, err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 template <int K>
-static cudaError_t launch_count_k(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols,
-                                  const CountPlan &plan, const CountStats &hs, const CountStats *st,
+static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const uint32_t *dag_cols,
+                                  const CountStats &hs, const CountStats *st,
                                   const uint32_t *small_list, const uint32_t *mid_list,
                                   const uint32_t *big_list, uint32_t *next, uint32_t *list_scratch,
                                   size_t list_scratch_words, unsigned long long *result,
-                                  unsigned long long *per_root, uint32_t *err, cudaStream_t s,
+                                  unsigned long long *work, uint32_t *err, cudaStream_t s,
                                   int num_sms)
 {
     cudaError_t e = cudaSuccess;
+    const CountPlan &plan = run.plan;
     if (hs.n_mid) {
         const uint32_t dcap = (hs.max_mid + 31) & ~31u;
         const uint32_t rs = (dcap / 32) | 1;
-        const size_t smem = ((size_t)dcap + (K > 3 ? (size_t)dcap * rs : 0)) * sizeof(uint32_t);
-        const int threads = plan.warps_per_cta * 32;
-        if ((e = cudaFuncSetAttribute(k_count_mid<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)))
+        int smem_cap = 0, dev = 0;
+        cudaGetDevice(&dev);
+        if ((e = cudaDeviceGetAttribute(&smem_cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)))
             return e;
-        int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_mid<K>, threads,
-                                                               smem)))
-            return e;
-        if (per_sm < 1) per_sm = 1;
-        uint32_t grid = (uint32_t)(num_sms * per_sm);
-        if (grid > hs.n_mid) grid = hs.n_mid;
-        k_count_mid<K><<<grid, threads, smem, s>>>(dag_off, dag_cols, mid_list, st, next + 0, dcap,
-                                                   result, per_root, err);
-        if ((e = cudaGetLastError())) return e;
+        smem_cap -= 1024;  // static shared memory of the kernel
+        auto smem_for = [&](uint32_t warps) {
+            return ((size_t)dcap +
+                    (K > 3 ? (size_t)dcap * rs + (size_t)warps * warp_scratch_words(dcap) : 0)) *
+                   sizeof(uint32_t);
+        };
+        uint32_t warps = plan.warps_per_cta > (uint32_t)kMidMaxWarps ? kMidMaxWarps : plan.warps_per_cta;
+        while (warps > 1 && smem_for(warps) > (size_t)smem_cap) warps--;
+        Timer t(run.time_kernels, s);
+        if (run.count_work)
+            e = launch_mid<K, true>(hs.n_mid, dcap, warps, smem_for(warps), dag_off, dag_cols,
+                                    mid_list, st, next + 0, result, run.per_root, work, err, s,
+                                    num_sms);
+        else
+            e = launch_mid<K, false>(hs.n_mid, dcap, warps, smem_for(warps), dag_off, dag_cols,
+                                     mid_list, st, next + 0, result, run.per_root, work, err, s,
+                                     num_sms);
+        if (e) return e;
+        t.stop();
+        run.kernel_ms[1] = t.ms();
     }
     if (hs.n_small) {
         uint32_t grid = (hs.n_small + kSmallWarps - 1) / kSmallWarps;
         const uint32_t cap = (uint32_t)num_sms * 16;
         if (grid > cap) grid = cap;
+        Timer t(run.time_kernels, s);
         k_count_small<K><<<grid, kSmallWarps * 32, 0, s>>>(dag_off, dag_cols, small_list, st, result,
-                                                           per_root, err);
+                                                           run.per_root, err);
+        note_launches(1);
         if ((e = cudaGetLastError())) return e;
+        t.stop();
+        run.kernel_ms[0] = t.ms();
     }
     if (hs.n_big) {
         const size_t per_warp = (size_t)hs.max_big * (K > 3 ? K - 3 : 1);
@@ -510,20 +714,23 @@ static cudaError_t launch_count_k(uint32_t n, const uint64_t *dag_off, const uin
         const uint32_t cap = (uint32_t)num_sms;
         if (grid > cap) grid = cap;
         if (grid > (hs.n_big + kListWarps - 1) / kListWarps) grid = (hs.n_big + kListWarps - 1) / kListWarps;
+        Timer t(run.time_kernels, s);
         k_count_list<K><<<grid, kListWarps * 32, 0, s>>>(dag_off, dag_cols, big_list, st, next + 1,
-                                                         list_scratch, hs.max_big, result, per_root,
-                                                         err);
+                                                         list_scratch, hs.max_big, result,
+                                                         run.per_root, err);
+        note_launches(1);
         if ((e = cudaGetLastError())) return e;
+        t.stop();
+        run.kernel_ms[2] = t.ms();
     }
     return cudaSuccess;
 }
 
 // Runs the count for k >= 3.  Returns a CUDA error, or cudaErrorMemoryAllocation when the
-// workspace is too small.  The host value lands in *h_result; device errors in *h_err.
+// workspace is too small.  The host value lands in *h_result.
 cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
-                      uint32_t max_outdeg, const CountPlan &plan, unsigned long long *per_root,
-                      uint32_t *err, Carver &c, cudaStream_t s, int num_sms,
-                      unsigned long long *h_result, uint32_t *h_err)
+                      CountRun &run, uint32_t *err, Carver &c, cudaStream_t s, int num_sms,
+                      unsigned long long *h_result)
 {
     CountStats *st = c.take<CountStats>(1);
     unsigned long long *result = c.take<unsigned long long>(2);
@@ -537,7 +744,8 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
     // the rest of the workspace is list-path scratch
     uint32_t *list_scratch = (uint32_t *)(c.base + c.used);
     const size_t list_words = c.cap > c.used ? (c.cap - c.used) / sizeof(uint32_t) : 0;
-    (void)max_outdeg;
+    unsigned long long *work = result + 1;
+    const CountPlan &plan = run.plan;
 
     cudaError_t e;
     if ((e = cudaMemsetAsync(st, 0, sizeof(CountStats), s))) return e;
@@ -548,19 +756,19 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
     const uint32_t blocks = (n + 255) / 256;
     if (n) {
         k_classify<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max,
-                                          small_list, big_list, hist, st, per_root);
+                                          small_list, big_list, hist, st, run.per_root);
         k_mid_bins<<<1, 1024, 0, s>>>(hist, plan.bitmap_max + 1, cursor, st);
         k_mid_scatter<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max,
                                              cursor, mid_list);
+        note_launches(3);
     }
     CountStats hs;
     if ((e = cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s))) return e;
     if ((e = cudaStreamSynchronize(s))) return e;
-#define CITRON_CASE(KK)                                                                          \
-    case KK:                                                                                     \
-        e = launch_count_k<KK>(n, dag_off, dag_cols, plan, hs, st, small_list, mid_list,         \
-                               big_list, next, list_scratch, list_words, result, per_root, err, \
-                               s, num_sms);                                                      \
+#define CITRON_CASE(KK)                                                                           \
+    case KK:                                                                                      \
+        e = launch_count_k<KK>(run, dag_off, dag_cols, hs, st, small_list, mid_list, big_list,    \
+                               next, list_scratch, list_words, result, work, err, s, num_sms);    \
         break;
     switch (k) {
         CITRON_CASE(3)
@@ -577,16 +785,21 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
     }
 #undef CITRON_CASE
     if (e) return e;
-    if ((e = cudaMemcpyAsync(h_result, result, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)))
-        return e;
-    if ((e = cudaMemcpyAsync(h_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return e;
-    return cudaStreamSynchronize(s);
+    unsigned long long out[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(out, result, sizeof(out), cudaMemcpyDeviceToHost, s))) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    *h_result = out[0];
+    run.work = out[1];
+    return cudaSuccess;
 }
 
 cudaError_t launch_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
                                     unsigned long long *per_root, cudaStream_t s)
 {
-    if (n) k_per_root_trivial<<<(n + 255) / 256, 256, 0, s>>>(n, dag_off, k, per_root);
+    if (n) {
+        k_per_root_trivial<<<(n + 255) / 256, 256, 0, s>>>(n, dag_off, k, per_root);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 

@@ -574,6 +574,7 @@ cudaError_t launch_order(uint32_t n, const uint64_t *off, uint32_t *rank, uint32
         uint32_t *vout = last ? (perm ? perm : vals[p & 1]) : vals[p & 1];
         k_radix_scatter<<<nb, kRsThreads, 0, st>>>(off, kin, vin, n, 8 * p, hist, nb, kout, vout,
                                                    last ? rank : nullptr);
+        note_launches(3);
         kin = kout;
         vin = vout;
     }
@@ -620,7 +621,11 @@ cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, con
         const int vec4 = ((uintptr_t)cols % 16) == 0;
         k_gen_ordering<<<ntiles, kGoThreads, 0, st>>>(n, arcs, off, cols, first_row, ntiles, dag_off,
                                                      dag_cols, arcs / 2, status, ctr, err, vec4);
-        if (d_max_outdeg) k_max_rowlen<<<num_sms * 4, 256, 0, st>>>(n, dag_off, d_max_outdeg);
+        note_launches(2);
+        if (d_max_outdeg) {
+            k_max_rowlen<<<num_sms * 4, 256, 0, st>>>(n, dag_off, d_max_outdeg);
+            note_launches(1);
+        }
         return cudaGetLastError();
     }
     if ((e = cudaMemsetAsync(sc_status, 0, ((size_t)sc_tiles + 1) * sizeof(unsigned long long), st)))
@@ -638,6 +643,7 @@ cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, con
         return e;
     k_fill_rank_long<<<num_sms, 1024, cap_bytes, st>>>(n, off, cols, rank, dag_off, dag_cols,
                                                        long_rows, n_long, kLongCap, err);
+    note_launches(4);
     if (d_max_outdeg)
         if ((e = cudaMemcpyAsync(d_max_outdeg, max_len, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)))
             return e;
@@ -648,6 +654,7 @@ cudaError_t launch_validate(uint32_t n, uint64_t arcs, const uint64_t *off, cons
                             uint32_t *bad, cudaStream_t st, int num_sms)
 {
     k_validate<<<num_sms * 8, 256, 0, st>>>(n, arcs, off, cols, bad);
+    note_launches(1);
     return cudaGetLastError();
 }
 

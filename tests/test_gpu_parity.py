@@ -116,9 +116,12 @@ def test_per_root_counts(gpu, oracle_lib, graphs, path):
 
 
 def test_closed_forms(gpu):
+    # (n, k) pairs whose enumeration stays small: C(n, k-1) leaf sets at most ~1e9
     for n in (1, 2, 5, 32, 33, 64, 200):
         G = gpu.DeviceGraph(gg.complete(n))
         for k in range(1, min(n + 2, 11)):
+            if math.comb(n, k - 1) > 1e9:
+                break
             assert G.count(k) == math.comb(n, k), (n, k)
     G = gpu.DeviceGraph(gg.cocktail_party(14))
     for k in range(1, 13):
