@@ -284,6 +284,39 @@ __device__ __forceinline__ uint32_t compact(const WarpCtx &x, uint32_t c, int la
     return total;
 }
 
+// Triangular layout only (every row holds bits above its own index).  Sum over the members
+// b = elem[j], j in [j0, total), that lie in the candidate words cw (broadcast-readable shared
+// words) of |cw ∧ row_b|, restricted to words below hi.  Members are taken 32 at a time in
+// index order; within such a round every lane loops over the same words [word(first), hi):
+// rows have no bits below their own word, so the lanes whose member starts higher only add
+// zeros, and the loop stays uniform (no divergence).  Consecutive members sit in different
+// banks because the row stride is odd.  MASK: members outside cw contribute nothing.
+template <bool MASK, bool WORK>
+__device__ __forceinline__ uint32_t tri_rounds(const WarpCtx &x, const uint32_t *cw, uint32_t j0,
+                                               uint32_t total, int hi, int lane,
+                                               unsigned long long &work)
+{
+    uint32_t s = 0;
+    const uint32_t lim = (uint32_t)hi << 5;
+    for (; j0 < total; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const uint32_t b = j < total ? x.elem[j] : 0xffffu;
+        const uint32_t first = __shfl_sync(kFull, b, 0);
+        if (first >= lim) break;
+        bool in = b < lim;
+        if (MASK && in) in = (cw[b >> 5] >> (b & 31)) & 1;
+        if (WORK && in) work += (uint32_t)(hi - (int)(b >> 5));
+        const uint32_t *rb = x.rows + (in ? b : first) * x.RS;
+        int w = (int)(first >> 5);
+        for (; w + 1 < hi; w += 2) {
+            const uint32_t r0 = in ? rb[w] : 0u, r1 = in ? rb[w + 1] : 0u;
+            s += __popc(cw[w] & r0) + __popc(cw[w + 1] & r1);
+        }
+        if (w < hi) s += __popc(cw[w] & (in ? rb[w] : 0u));
+    }
+    return s;
+}
+
 // Counts the R-cliques inside the candidate set whose word w sits in lane w (words >= W are
 // zero); adds lane-partial sums to acc.
 //   R >= 4: warp-uniform walk over the members a; the next candidate set c ∧ row_a is again
@@ -317,6 +350,11 @@ __device__ __forceinline__ void warp_dfs(const WarpCtx &x, uint32_t c, int lane,
                 }
             }
             acc += s;
+            __syncwarp();
+        } else if (x.tri) {
+            int clo, chi;
+            const uint32_t total = compact(x, c, lane, clo, chi);
+            acc += tri_rounds<false, WORK>(x, x.cbuf, 0, total, chi, lane, work);
             __syncwarp();
         } else {
             int clo, chi;

@@ -164,9 +164,11 @@ def test_edge_cases(gpu, oracle_lib):
     # k above max out-degree + 1 is zero; k = 12 (largest supported) on K_14
     G = gpu.DeviceGraph(gg.complete(14))
     assert G.count(12) == math.comb(14, 12)
-    g = gg.small_rmat(30, 3000, 10.0)
+    g = gg.small_er(30, 3000, 3.0)
     G = gpu.DeviceGraph(g)
-    assert G.count(G.max_outdeg + 2) == 0
+    assert G.max_outdeg + 2 <= 12
+    for k in range(G.max_outdeg + 2, 13):
+        assert G.count(k) == 0
 
 
 def test_invalid_arguments(gpu):
