@@ -158,6 +158,28 @@ citron_status citron_count_host(uint32_t n, uint64_t arcs, const uint64_t *h_off
                                 uint64_t *h_counts, void *d_buf, size_t buf_bytes, void *ws,
                                 size_t ws_bytes, void *stream);
 
+/*
+ * citron_count_noalloc -- citron_count for callers that cannot allocate device memory.  (The
+ * paper has no counterpart: this is an interface choice of this library.)
+ *   Who needs it: code running while a stream is captured into a CUDA graph (allocation is not
+ *   allowed there), host applications or plugin frameworks that own the device heap and forbid
+ *   allocation after start-up, real-time loops that cannot take the implicit synchronisation of
+ *   cudaMalloc/cudaFree, and C callers with no allocator of their own.  They still pass the DAG
+ *   (input) and receive the count (output); no workspace is needed.
+ *   How: the scratch lives in one fixed file-scope device array of 1 MiB that every GPU loading
+ *   this library holds until the process exits.  No cudaMalloc, cudaFree or allocating library
+ *   routine is called.  The first call on a device (with that device current) looks up the
+ *   array's device address; make that first call before any stream capture.
+ *   Limits: n <= 65536 vertices (larger n returns CITRON_E_UNSUPPORTED); roots with out-degree
+ *   above 1024 take the sorted-list path, whose scratch may not fit (CITRON_E_WORKSPACE).
+ *   Every call shares the one array and clears what it needs: calls that overlap on the GPU
+ *   (different streams or threads on the same device) race and must not be issued.
+ *   Same arguments and results as citron_count otherwise.  Synchronises `stream`.
+ */
+citron_status citron_count_noalloc(uint32_t n, const uint64_t *d_dag_off,
+                                   const uint32_t *d_dag_cols, uint32_t k, uint64_t *h_count,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

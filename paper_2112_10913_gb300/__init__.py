@@ -39,6 +39,7 @@ EXPORTS = (
     "citron_kernel_launches",
     "citron_host_buffer_bytes",
     "citron_count_host",
+    "citron_count_noalloc",
 )
 
 COUNT_TIME_KERNELS = 1
@@ -101,6 +102,8 @@ def lib() -> ctypes.CDLL:
     L.citron_host_buffer_bytes.restype = sz
     L.citron_count_host.argtypes = [u32, u64, vp, vp, vp, u32, vp, vp, sz, vp, sz, vp]
     L.citron_count_host.restype = i32
+    L.citron_count_noalloc.argtypes = [u32, vp, vp, u32, vp, vp]
+    L.citron_count_noalloc.restype = i32
     _lib = L
     return L
 
@@ -194,6 +197,14 @@ def citron_count_ex(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, 
                                  ctypes.byref(out), _dptr(ws), _nbytes(ws), _stream(stream)),
            f"citron_count_ex(k={k})")
     return int(out.value), o
+
+
+def citron_count_noalloc(n: int, dag_off, dag_cols, k: int, stream=None) -> int:
+    """citron_count without a workspace (fixed device scratch; n <= 65536)."""
+    out = ctypes.c_uint64(0)
+    _check(lib().citron_count_noalloc(n, _dptr(dag_off), _dptr(dag_cols), k, ctypes.byref(out),
+                                      _stream(stream)), f"citron_count_noalloc(k={k})")
+    return int(out.value)
 
 
 def citron_kernel_launches() -> int:

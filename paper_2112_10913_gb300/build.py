@@ -15,7 +15,7 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 OUT_DIR = PKG / "_build"
 LIB = PKG / "libcitron.so"
-SOURCES = ["api.cu", "order.cu", "count.cu"]
+SOURCES = ["api.cu", "order.cu", "count.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
 
