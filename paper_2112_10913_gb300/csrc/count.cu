@@ -229,6 +229,8 @@ __global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
 //   cbuf : the current candidate set's words
 //   lbuf : one candidate set per lane, word-major ([w * 32 + lane]), so that lanes reading
 //          their own word w always hit 32 different banks
+constexpr uint32_t kCompactMax = 128;  // largest candidate set re-encoded compactly
+
 struct WarpCtx {
     const uint32_t *rows;
     uint32_t RS, W;
@@ -236,6 +238,8 @@ struct WarpCtx {
     uint16_t *elem;
     uint32_t *cbuf;
     uint32_t *lbuf;
+    uint32_t *mv;    // compress masks: 5 per candidate word, then the member prefix per word
+    uint32_t *mbuf;  // compact rows, 4 words each (16-byte aligned); aliases lbuf
 };
 
 // Number of DAG arcs inside the lane's own candidate set lb (words [lo, hi)): the penultimate
@@ -317,6 +321,219 @@ __device__ __forceinline__ uint32_t tri_rounds(const WarpCtx &x, const uint32_t 
     return s;
 }
 
+// ---- Compact re-encoding of a small candidate set ------------------------------------------
+// A candidate set with s <= 128 members (listed in elem) is re-encoded as the s x s adjacency of
+// its induced sub-DAG, row i = the members j that are out-neighbours of member i, packed into 4
+// words ("compact rows"; upper-triangular when the DAG is relabelled to its order).  The remaining
+// levels of the recursion then work on at most 4 words per set instead of the root-wide span.
+//
+// Bits are gathered word by word with the parallel-suffix "compress" of H. S. Warren, Hacker's
+// Delight (2nd ed., Sec. 7-4): for a mask m the five move masks depend on m only, so they are
+// computed once per candidate word (lane-parallel) and shared by every row.
+__device__ __forceinline__ void compress_masks(uint32_t m, uint32_t mv[5])
+{
+    uint32_t mk = ~m << 1;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        uint32_t mp = mk ^ (mk << 1);
+        mp ^= mp << 2;
+        mp ^= mp << 4;
+        mp ^= mp << 8;
+        mp ^= mp << 16;
+        const uint32_t v = mp & m;
+        mv[i] = v;
+        m = (m ^ v) | (v >> (1 << i));
+        mk &= ~mp;
+    }
+}
+
+__device__ __forceinline__ uint32_t compress_with(uint32_t x, uint32_t m, const uint32_t *mv)
+{
+    x &= m;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const uint32_t t = x & mv[i];
+        x = (x ^ t) | (t >> (1 << i));
+    }
+    return x;
+}
+
+// Builds the compact rows of the s members of the candidate set (words in cbuf, members in
+// elem, non-zero words [clo, chi)) into mbuf[i * 4 + q].
+__device__ __forceinline__ void build_compact(const WarpCtx &x, uint32_t s, int clo, int chi, int lane)
+{
+    // per candidate word w (lane w): compress masks and the number of members before word w
+    {
+        const uint32_t m = (lane < chi && lane >= clo) ? x.cbuf[lane] : 0u;
+        uint32_t mv[5];
+        compress_masks(m, mv);
+        const uint32_t pc = __popc(m);
+        const uint32_t pre = warp_incl_scan(pc) - pc;
+#pragma unroll
+        for (int i = 0; i < 5; i++) x.mv[i * 32 + lane] = mv[i];
+        x.mv[160 + lane] = pre;
+    }
+    __syncwarp();
+    for (uint32_t i0 = 0; i0 < s; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const bool act = i < s;
+        const uint32_t ei = act ? x.elem[i] : x.elem[i0];
+        const uint32_t *row = x.rows + ei * x.RS;
+        uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+        // triangular rows hold bits above their own member only: start at the word of the
+        // round's first member
+        for (int w = x.tri ? (int)(x.elem[i0] >> 5) : clo; w < chi; w++) {
+            const uint32_t m = x.cbuf[w];
+            if (!m) continue;
+            uint32_t mv[5];
+#pragma unroll
+            for (int t = 0; t < 5; t++) mv[t] = x.mv[t * 32 + w];
+            const uint32_t pre = x.mv[160 + w];
+            const uint32_t piece = compress_with(row[w], m, mv);
+            const uint32_t q = pre >> 5, sh = pre & 31;
+            const uint32_t lo = piece << sh, hi = sh ? (piece >> (32 - sh)) : 0u;
+            o0 |= q == 0 ? lo : 0u;
+            o1 |= q == 1 ? lo : (q == 0 ? hi : 0u);
+            o2 |= q == 2 ? lo : (q == 1 ? hi : 0u);
+            o3 |= q == 3 ? lo : (q == 2 ? hi : 0u);
+        }
+        if (act) reinterpret_cast<uint4 *>(x.mbuf)[i] = make_uint4(o0, o1, o2, o3);
+    }
+    __syncwarp();
+}
+
+// Sum of popc(a[w] & b[w]) over words w in [FROM, CW).
+template <int CW, int FROM>
+__device__ __forceinline__ uint32_t popc_and(const uint32_t (&a)[CW], const uint4 &b)
+{
+    uint32_t s = 0;
+    if (FROM <= 0) s += __popc(a[0] & b.x);
+    if (CW > 1 && FROM <= 1) s += __popc(a[1] & b.y);
+    if (CW > 2 && FROM <= 2) s += __popc(a[2] & b.z);
+    if (CW > 3 && FROM <= 3) s += __popc(a[3] & b.w);
+    return s;
+}
+
+// Word q of the members' bits: for R = 2 and 3 lanes take the members of word q (lane l <->
+// member 32q + l).  TRI: compact rows are upper-triangular, so a member's row (and any set
+// derived from it) has no bits in words below the member's own word; those words are skipped
+// at compile time.
+template <int R, int CW, bool TRI, bool WORK, int Q>
+__device__ __forceinline__ void cdfs_word(const uint4 *M, const uint32_t (&C)[CW], int lane,
+                                          uint32_t &s, unsigned long long &work)
+{
+    if constexpr (Q < CW) {
+        if ((C[Q] >> lane) & 1) {
+            const uint4 mi = M[Q * 32 + lane];
+            if constexpr (R == 2) {
+                s += popc_and<CW, TRI ? Q : 0>(C, mi);
+                if (WORK) work += TRI ? CW - Q : CW;
+            } else {
+                uint32_t D[CW];
+                D[0] = C[0] & mi.x;
+                if (CW > 1) D[1] = C[1] & mi.y;
+                if (CW > 2) D[2] = C[2] & mi.z;
+                if (CW > 3) D[3] = C[3] & mi.w;
+#pragma unroll
+                for (int q2 = TRI ? Q : 0; q2 < CW; q2++) {
+                    uint32_t y = D[q2];
+                    if (WORK) work += (unsigned long long)__popc(y) * (TRI ? CW - q2 : CW);
+                    while (y) {
+                        const uint32_t j = (uint32_t)(q2 << 5) + __ffs(y) - 1;
+                        y &= y - 1;
+                        const uint4 mj = M[j];
+                        if (!TRI) s += popc_and<CW, 0>(D, mj);
+                        else if (q2 == 0) s += popc_and<CW, 0>(D, mj);
+                        else if (q2 == 1) s += popc_and<CW, 1>(D, mj);
+                        else if (q2 == 2) s += popc_and<CW, 2>(D, mj);
+                        else s += popc_and<CW, 3>(D, mj);
+                    }
+                }
+            }
+        }
+        cdfs_word<R, CW, TRI, WORK, Q + 1>(M, C, lane, s, work);
+    }
+}
+
+// R-cliques inside the compact set C (CW words, the same on every lane); rows in mbuf.
+template <int R, int CW, bool TRI, bool WORK>
+__device__ __forceinline__ void cdfs(const WarpCtx &x, const uint32_t (&C)[CW], int lane,
+                                     unsigned long long &acc, unsigned long long &work)
+{
+    const uint4 *M = reinterpret_cast<const uint4 *>(x.mbuf);
+    if constexpr (R == 1) {
+        if (lane == 0) {
+            uint32_t t = 0;
+#pragma unroll
+            for (int q = 0; q < CW; q++) t += __popc(C[q]);
+            acc += t;
+        }
+    } else if constexpr (R == 2 || R == 3) {
+        uint32_t s = 0;
+        cdfs_word<R, CW, TRI, WORK, 0>(M, C, lane, s, work);
+        acc += s;
+    } else {
+        // members in order; one recursive call site per level keeps the code linear in R
+        uint32_t rem[CW];
+#pragma unroll
+        for (int t = 0; t < CW; t++) rem[t] = C[t];
+        for (;;) {
+            int q = -1;
+            uint32_t word = 0;
+#pragma unroll
+            for (int t = CW - 1; t >= 0; t--)
+                if (rem[t]) {
+                    q = t;
+                    word = rem[t];
+                }
+            if (q < 0) break;
+            const uint32_t i = (uint32_t)(q << 5) + __ffs(word) - 1;
+#pragma unroll
+            for (int t = 0; t < CW; t++)
+                if (t == q) rem[t] &= rem[t] - 1;
+            const uint4 mi = M[i];
+            uint32_t C2[CW];
+            C2[0] = C[0] & mi.x;
+            if (CW > 1) C2[1] = C[1] & mi.y;
+            if (CW > 2) C2[2] = C[2] & mi.z;
+            if (CW > 3) C2[3] = C[3] & mi.w;
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int t = 0; t < CW; t++) cnt += __popc(C2[t]);
+            if (WORK && lane == 0) work += CW;
+            if (cnt >= R - 1) cdfs<R - 1, CW, TRI, WORK>(x, C2, lane, acc, work);
+        }
+    }
+}
+
+template <int R, int CW, bool TRI, bool WORK>
+__device__ __forceinline__ void cdfs_all(const WarpCtx &x, uint32_t s, int lane,
+                                         unsigned long long &acc, unsigned long long &work)
+{
+    uint32_t C[CW];
+#pragma unroll
+    for (int q = 0; q < CW; q++) {
+        const uint32_t lo = q * 32;
+        C[q] = s >= lo + 32 ? kFull : (s > lo ? ((1u << (s - lo)) - 1) : 0u);
+    }
+    cdfs<R, CW, TRI, WORK>(x, C, lane, acc, work);
+}
+
+// Entry for a candidate set of at most 128 members (lane word c), triangular layout.
+template <int R, bool WORK>
+__device__ __forceinline__ void compact_entry(const WarpCtx &x, uint32_t c, int lane,
+                                              unsigned long long &acc, unsigned long long &work)
+{
+    int clo, chi;
+    const uint32_t s = compact(x, c, lane, clo, chi);
+    build_compact(x, s, clo, chi, lane);
+    if (s <= 32) cdfs_all<R, 1, true, WORK>(x, s, lane, acc, work);
+    else if (s <= 64) cdfs_all<R, 2, true, WORK>(x, s, lane, acc, work);
+    else if (s <= 96) cdfs_all<R, 3, true, WORK>(x, s, lane, acc, work);
+    else cdfs_all<R, 4, true, WORK>(x, s, lane, acc, work);
+    __syncwarp();
+}
+
 // Counts the R-cliques inside the candidate set whose word w sits in lane w (words >= W are
 // zero); adds lane-partial sums to acc.
 //   R >= 4: warp-uniform walk over the members a; the next candidate set c ∧ row_a is again
@@ -328,6 +545,12 @@ template <int R, bool WORK>
 __device__ __forceinline__ void warp_dfs(const WarpCtx &x, uint32_t c, int lane,
                                          unsigned long long &acc, unsigned long long &work)
 {
+    if constexpr (R >= 3) {
+        if (x.tri && __reduce_add_sync(kFull, __popc(c)) <= kCompactMax) {
+            compact_entry<R, WORK>(x, c, lane, acc, work);
+            return;
+        }
+    }
     if constexpr (R == 1) {
         acc += __popc(c);
     } else if constexpr (R == 2) {
@@ -411,9 +634,10 @@ __device__ __forceinline__ void warp_dfs(const WarpCtx &x, uint32_t c, int lane,
 }
 
 // Shared-memory words one warp needs for roots of out-degree <= dcap (dcap multiple of 32).
+// Layout: elem (dcap uint16) | cbuf (32) | compress masks + prefixes (192) | lbuf/mbuf.
 __host__ __device__ __forceinline__ uint32_t warp_scratch_words(uint32_t dcap)
 {
-    return dcap / 2 + 32 + 32 * (dcap / 32);
+    return dcap / 2 + 32 + 192 + (dcap > 512 ? dcap : 512);
 }
 
 constexpr int kMidMaxWarps = 32;
@@ -425,7 +649,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     unsigned long long *result, unsigned long long *per_root, unsigned long long *work_out,
     uint32_t *err)
 {
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t rs_cap = (dcap / 32) | 1;
     uint32_t *sL = smem;
     uint32_t *rows = smem + dcap;
@@ -437,7 +661,9 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     x.rows = rows;
     x.elem = reinterpret_cast<uint16_t *>(wscr);
     x.cbuf = wscr + dcap / 2;
-    x.lbuf = wscr + dcap / 2 + 32;
+    x.mv = wscr + dcap / 2 + 32;
+    x.lbuf = wscr + dcap / 2 + 32 + 192;
+    x.mbuf = x.lbuf;
     const uint32_t nlist = st->n_mid;
     unsigned long long block_total = 0;  // meaningful in thread 0
     for (;;) {
