@@ -133,6 +133,9 @@ typedef struct {
     uint32_t warps_per_cta;  /* in: warps per bitmap-path block, 1..32 (0: 32); fewer are used
                                 when the block's shared memory would not fit */
     uint32_t flags;          /* in: CITRON_COUNT_* bits */
+    uint32_t compact_max;    /* in: candidate sets of the bitmap path with at most this many
+                                members are re-encoded as compact bitmaps: 0 or 128 mean 128,
+                                1 means never */
     uint64_t *d_per_root;    /* in: optional device array of n uint64, as in citron_count */
     uint64_t work_ops;       /* out: 32-bit AND+POPC word operations of the bitmap path */
     float kernel_ms[3];      /* out: device ms of the warp-register, bitmap, sorted-list kernels */

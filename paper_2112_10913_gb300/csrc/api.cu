@@ -194,10 +194,13 @@ citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint3
     if (k > CITRON_MAX_K) return CITRON_E_UNSUPPORTED;
     if (opts->small_max > 32 || opts->bitmap_max > 1024 || opts->warps_per_cta > 32)
         return CITRON_E_INVALID;
+    if (opts->compact_max != 0 && opts->compact_max != 1 && opts->compact_max != 128)
+        return CITRON_E_INVALID;
     CountRun run;
     if (opts->small_max) run.plan.small_max = opts->small_max;
     if (opts->bitmap_max) run.plan.bitmap_max = opts->bitmap_max;
     if (opts->warps_per_cta) run.plan.warps_per_cta = opts->warps_per_cta;
+    if (opts->compact_max) run.plan.compact_max = opts->compact_max == 1 ? 0 : opts->compact_max;
     if (run.plan.bitmap_max < run.plan.small_max) run.plan.bitmap_max = run.plan.small_max;
     run.per_root = (unsigned long long *)opts->d_per_root;
     run.time_kernels = (opts->flags & CITRON_COUNT_TIME_KERNELS) != 0;

@@ -1,0 +1,903 @@
+// count_impl.cuh -- device templates of the counting phase (included by count.cu and by the
+// per-k translation units count_k*.cu, which instantiate them in parallel builds).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace citron {
+
+
+constexpr int kMaxK = CITRON_MAX_K;
+constexpr uint32_t kBitmapCap = 1024;  // largest root handled by the bitmap path
+constexpr int kSmallWarps = 8;         // warps per block of k_count_small
+constexpr int kListWarps = 4;          // warps per block of k_count_list
+
+struct CountStats {
+    uint32_t n_small, n_mid, n_big;
+    uint32_t max_mid, max_big, max_all;
+    uint32_t pad[2];
+};
+
+// ------------------------------------------------------------------------------------------
+// Warp-register path (D <= 32).
+
+// Number of R-cliques inside the warp-uniform candidate mask `cand` (bit j = j-th out-neighbour
+// of the root); lane i holds row i of the local subgraph.  Adds lane-partial sums to acc.
+template <int R>
+__device__ __forceinline__ void small_dfs(uint32_t cand, uint32_t myrow, int lane,
+                                          unsigned long long &acc)
+{
+    if constexpr (R == 1) {
+        if (lane == 0) acc += __popc(cand);
+    } else if constexpr (R == 2) {
+        if ((cand >> lane) & 1) acc += __popc(cand & myrow);
+    } else {
+        uint32_t c = cand;
+        while (c) {
+            const int a = __ffs(c) - 1;
+            c &= c - 1;
+            const uint32_t c2 = cand & __shfl_sync(kFull, myrow, a);
+            if (__popc(c2) >= R - 1) small_dfs<R - 1>(c2, myrow, lane, acc);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t lower_bound_smem(const uint32_t *a, uint32_t n, uint32_t x)
+{
+    uint32_t lo = 0, len = n;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if (a[lo + half] < x) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
+template <int K>
+__global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
+    const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
+    const uint32_t *__restrict__ list, const CountStats *st, unsigned long long *result,
+    unsigned long long *per_root, uint32_t *err)
+{
+    __shared__ uint32_t sL[kSmallWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t nlist = st->n_small;
+    const uint32_t gw = blockIdx.x * kSmallWarps + w, nwarps = gridDim.x * kSmallWarps;
+    unsigned long long total = 0;
+    for (uint32_t idx = gw; idx < nlist; idx += nwarps) {
+        const uint32_t u = list[idx];
+        const uint64_t base = dag_off[u];
+        const uint32_t D = (uint32_t)(dag_off[u + 1] - base);
+        const uint32_t x = lane < D ? dag_cols[base + lane] : 0xffffffffu;
+        sL[w][lane] = x;
+        __syncwarp();
+        const uint32_t lmax = __shfl_sync(kFull, x, D - 1);
+        uint64_t rb = 0, re = 0;
+        if (lane < D) {
+            rb = dag_off[x];
+            re = dag_off[x + 1];
+        }
+        uint32_t myrow = 0;
+        for (uint32_t i = 0; i < D; i++) {
+            const uint64_t b = __shfl_sync(kFull, rb, i), e = __shfl_sync(kFull, re, i);
+            uint32_t bits = 0;
+            for (uint64_t p = b; p < e; p += 32) {
+                const uint32_t y = p + lane < e ? dag_cols[p + lane] : 0xffffffffu;
+                if (__shfl_sync(kFull, y, 0) > lmax) break;
+                if (y <= lmax) {
+                    const uint32_t j = lower_bound_smem(sL[w], D, y);
+                    if (sL[w][j] == y) bits |= 1u << j;
+                }
+            }
+            bits = __reduce_or_sync(kFull, bits);
+            if (lane == i) myrow = bits;
+        }
+        unsigned long long acc = 0;
+        const uint32_t all = D == 32 ? kFull : ((1u << D) - 1);
+        small_dfs<K - 1>(all, myrow, lane, acc);
+        if (per_root) {
+            const unsigned long long r = warp_sum_u64(acc, err);
+            if (lane == 0) per_root[u] = r;
+        }
+        total += acc;
+        __syncwarp();
+    }
+    total = warp_sum_u64(total, err);
+    if (lane == 0) add_checked(result, total, err);
+}
+
+// ------------------------------------------------------------------------------------------
+// Shared-memory bitmap path (small_max < D <= 1024).
+
+// Per-warp view of the block's local subgraph and the warp's private scratch.
+//   rows : D x RS words, row i = bits j with L[j] in N+(L[i]) (RS odd: column reads by
+//          different rows fall in different banks)
+//   tri  : every row only has bits above its own index (true for a DAG relabelled to ranks, whose
+//          rows are sorted in the DAG order); lets the loops skip the words below an element.
+//   elem : the current candidate set as a list of indices (compaction buffer)
+//   cbuf : the current candidate set's words
+//   lbuf : one candidate set per lane, word-major ([w * 32 + lane]), so that lanes reading
+//          their own word w always hit 32 different banks
+
+struct WarpCtx {
+    const uint32_t *rows;
+    uint32_t RS, W;
+    bool tri;
+    uint16_t *elem;
+    uint32_t *cbuf;
+    uint32_t *lbuf;
+    uint32_t *mv;    // compress masks: 5 per candidate word, then the member prefix per word
+    uint32_t *mbuf;  // compact rows, 4 words each (16-byte aligned); aliases lbuf
+    uint32_t compact_max;  // largest candidate set re-encoded compactly (0 or 128)
+};
+
+// Number of DAG arcs inside the lane's own candidate set lb (words [lo, hi)): the penultimate
+// level of Counting, which only adds subgraph degrees.  WORK adds the 32-bit word operations
+// (AND + POPC) performed to `work`.
+template <bool WORK>
+__device__ __forceinline__ uint32_t lane_arcs(const WarpCtx &x, const uint32_t *lb, int lo, int hi,
+                                              unsigned long long &work)
+{
+    uint32_t s = 0;
+    for (int w = lo; w < hi; w++) {
+        uint32_t y = lb[w * 32];
+        if (WORK) work += (unsigned long long)__popc(y) * (uint32_t)(hi - (x.tri ? w : lo));
+        while (y) {
+            const uint32_t b = (uint32_t)(w << 5) + __ffs(y) - 1;
+            y &= y - 1;
+            const uint32_t *rb = x.rows + b * x.RS;
+            int w2 = x.tri ? w : lo;
+            // two independent word pairs per step keep two shared-memory loads in flight
+            for (; w2 + 1 < hi; w2 += 2)
+                s += __popc(lb[w2 * 32] & rb[w2]) + __popc(lb[w2 * 32 + 32] & rb[w2 + 1]);
+            if (w2 < hi) s += __popc(lb[w2 * 32] & rb[w2]);
+        }
+    }
+    return s;
+}
+
+// Writes the candidate set (lane word c) to cbuf and its member indices to elem; returns the
+// member count and the range [clo, chi) of its non-zero words.
+__device__ __forceinline__ uint32_t compact(const WarpCtx &x, uint32_t c, int lane, int &clo, int &chi)
+{
+    const uint32_t pc = __popc(c);
+    const uint32_t incl = warp_incl_scan(pc);
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    uint32_t pos = incl - pc;
+    if (lane < (int)x.W) x.cbuf[lane] = c;
+    uint32_t y = c;
+    while (y) {
+        x.elem[pos++] = (uint16_t)((lane << 5) + __ffs(y) - 1);
+        y &= y - 1;
+    }
+    const uint32_t nz = __ballot_sync(kFull, c != 0);
+    clo = nz ? __ffs(nz) - 1 : 0;
+    chi = nz ? 32 - __clz(nz) : 0;
+    __syncwarp();
+    return total;
+}
+
+// Triangular layout only (every row holds bits above its own index).  Sum over the members
+// b = elem[j], j in [j0, total), that lie in the candidate words cw (broadcast-readable shared
+// words) of |cw ∧ row_b|, restricted to words below hi.  Members are taken 32 at a time in
+// index order; within such a round every lane loops over the same words [word(first), hi):
+// rows have no bits below their own word, so the lanes whose member starts higher only add
+// zeros, and the loop stays uniform (no divergence).  Consecutive members sit in different
+// banks because the row stride is odd.  MASK: members outside cw contribute nothing.
+template <bool MASK, bool WORK>
+__device__ __forceinline__ uint32_t tri_rounds(const WarpCtx &x, const uint32_t *cw, uint32_t j0,
+                                               uint32_t total, int hi, int lane,
+                                               unsigned long long &work)
+{
+    uint32_t s = 0;
+    const uint32_t lim = (uint32_t)hi << 5;
+    for (; j0 < total; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const uint32_t b = j < total ? x.elem[j] : 0xffffu;
+        const uint32_t first = __shfl_sync(kFull, b, 0);
+        if (first >= lim) break;
+        bool in = b < lim;
+        if (MASK && in) in = (cw[b >> 5] >> (b & 31)) & 1;
+        if (WORK && in) work += (uint32_t)(hi - (int)(b >> 5));
+        const uint32_t *rb = x.rows + (in ? b : first) * x.RS;
+        int w = (int)(first >> 5);
+        for (; w + 1 < hi; w += 2) {
+            const uint32_t r0 = in ? rb[w] : 0u, r1 = in ? rb[w + 1] : 0u;
+            s += __popc(cw[w] & r0) + __popc(cw[w + 1] & r1);
+        }
+        if (w < hi) s += __popc(cw[w] & (in ? rb[w] : 0u));
+    }
+    return s;
+}
+
+// ---- Compact re-encoding of a small candidate set ------------------------------------------
+// A candidate set with s <= 128 members (listed in elem) is re-encoded as the s x s adjacency of
+// its induced sub-DAG: row i = the members j that are out-neighbours of member i, packed into
+// CW = ceil(s/32) <= 4 words ("compact rows"; upper-triangular when the DAG is relabelled to its
+// order).  The remaining levels of the recursion then work on at most 4 words per set instead
+// of the root-wide span; a row is one 16-byte shared-memory load.  (Wider sets stay on the
+// root-wide bitmap: 8-word compact rows were measured slower on R-MAT 20.)
+//
+// Bits are gathered word by word with the parallel-suffix "compress" of H. S. Warren, Hacker's
+// Delight (2nd ed., Sec. 7-4): for a mask m the five move masks depend on m only, so they are
+// computed once per candidate word (lane-parallel) and shared by every row.
+__device__ __forceinline__ void compress_masks(uint32_t m, uint32_t mv[5])
+{
+    uint32_t mk = ~m << 1;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        uint32_t mp = mk ^ (mk << 1);
+        mp ^= mp << 2;
+        mp ^= mp << 4;
+        mp ^= mp << 8;
+        mp ^= mp << 16;
+        const uint32_t v = mp & m;
+        mv[i] = v;
+        m = (m ^ v) | (v >> (1 << i));
+        mk &= ~mp;
+    }
+}
+
+__device__ __forceinline__ uint32_t compress_with(uint32_t x, uint32_t m, const uint32_t *mv)
+{
+    x &= m;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const uint32_t t = x & mv[i];
+        x = (x ^ t) | (t >> (1 << i));
+    }
+    return x;
+}
+
+// Builds the compact rows of the s members of the candidate set (words in cbuf, members in
+// elem, non-zero words [clo, chi)).  NW = 4 or 8 output words per row.
+template <int NW>
+__device__ __forceinline__ void build_compact(const WarpCtx &x, uint32_t s, int clo, int chi, int lane)
+{
+    // per candidate word w (lane w): compress masks and the number of members before word w
+    {
+        const uint32_t m = (lane < chi && lane >= clo) ? x.cbuf[lane] : 0u;
+        uint32_t mv[5];
+        compress_masks(m, mv);
+        const uint32_t pc = __popc(m);
+        const uint32_t pre = warp_incl_scan(pc) - pc;
+#pragma unroll
+        for (int i = 0; i < 5; i++) x.mv[i * 32 + lane] = mv[i];
+        x.mv[160 + lane] = pre;
+    }
+    __syncwarp();
+    uint4 *out = reinterpret_cast<uint4 *>(x.mbuf);
+    for (uint32_t i0 = 0; i0 < s; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const bool act = i < s;
+        const uint32_t ei = act ? x.elem[i] : x.elem[i0];
+        const uint32_t *row = x.rows + ei * x.RS;
+        uint32_t o[NW];
+#pragma unroll
+        for (int t = 0; t < NW; t++) o[t] = 0;
+        // triangular rows hold bits above their own member only: start at the word of the
+        // round's first member
+        for (int w = x.tri ? (int)(x.elem[i0] >> 5) : clo; w < chi; w++) {
+            const uint32_t m = x.cbuf[w];
+            if (!m) continue;
+            uint32_t mv[5];
+#pragma unroll
+            for (int t = 0; t < 5; t++) mv[t] = x.mv[t * 32 + w];
+            const uint32_t pre = x.mv[160 + w];
+            const uint32_t piece = compress_with(row[w], m, mv);
+            const uint32_t q = pre >> 5, sh = pre & 31;
+            const uint32_t lo = piece << sh, hi = sh ? (piece >> (32 - sh)) : 0u;
+#pragma unroll
+            for (int t = 0; t < NW; t++) o[t] |= (q == (uint32_t)t ? lo : 0u) | (q + 1 == (uint32_t)t ? hi : 0u);
+        }
+        if (act) {
+            if (NW == 4) {
+                out[i] = make_uint4(o[0], o[1], o[2], o[3]);
+            } else {
+                out[2 * i] = make_uint4(o[0], o[1], o[2], o[3]);
+                out[2 * i + 1] = make_uint4(o[4 % NW], o[5 % NW], o[6 % NW], o[7 % NW]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Sum of popc(a[w] & b[w]) over words w in [FROM, CW).
+template <int CW, int FROM>
+__device__ __forceinline__ uint32_t popc_and(const uint32_t (&a)[CW], const uint4 &b)
+{
+    uint32_t s = 0;
+    if (FROM <= 0) s += __popc(a[0] & b.x);
+    if (CW > 1 && FROM <= 1) s += __popc(a[1] & b.y);
+    if (CW > 2 && FROM <= 2) s += __popc(a[2] & b.z);
+    if (CW > 3 && FROM <= 3) s += __popc(a[3] & b.w);
+    return s;
+}
+
+// Word q of the members' bits: for R = 2 and 3 lanes take the members of word q (lane l <->
+// member 32q + l).  TRI: compact rows are upper-triangular, so a member's row (and any set
+// derived from it) has no bits in words below the member's own word; those words are skipped
+// at compile time.
+template <int R, int CW, bool TRI, bool WORK, int Q>
+__device__ __forceinline__ void cdfs_word(const uint4 *M, const uint32_t (&C)[CW], int lane,
+                                          uint32_t &s, unsigned long long &work)
+{
+    if constexpr (Q < CW) {
+        if ((C[Q] >> lane) & 1) {
+            const uint4 mi = M[Q * 32 + lane];
+            if constexpr (R == 2) {
+                s += popc_and<CW, TRI ? Q : 0>(C, mi);
+                if (WORK) work += TRI ? CW - Q : CW;
+            } else {
+                uint32_t D[CW];
+                D[0] = C[0] & mi.x;
+                if (CW > 1) D[1] = C[1] & mi.y;
+                if (CW > 2) D[2] = C[2] & mi.z;
+                if (CW > 3) D[3] = C[3] & mi.w;
+#pragma unroll
+                for (int q2 = TRI ? Q : 0; q2 < CW; q2++) {
+                    uint32_t y = D[q2];
+                    if (WORK) work += (unsigned long long)__popc(y) * (TRI ? CW - q2 : CW);
+                    while (y) {
+                        const uint32_t j = (uint32_t)(q2 << 5) + __ffs(y) - 1;
+                        y &= y - 1;
+                        const uint4 mj = M[j];
+                        if (!TRI) s += popc_and<CW, 0>(D, mj);
+                        else if (q2 == 0) s += popc_and<CW, 0>(D, mj);
+                        else if (q2 == 1) s += popc_and<CW, 1>(D, mj);
+                        else if (q2 == 2) s += popc_and<CW, 2>(D, mj);
+                        else s += popc_and<CW, 3>(D, mj);
+                    }
+                }
+            }
+        }
+        cdfs_word<R, CW, TRI, WORK, Q + 1>(M, C, lane, s, work);
+    }
+}
+
+// R-cliques inside the compact set C (CW words, the same on every lane); rows in mbuf.
+template <int R, int CW, bool TRI, bool WORK>
+__device__ __forceinline__ void cdfs(const WarpCtx &x, const uint32_t (&C)[CW], int lane,
+                                     unsigned long long &acc, unsigned long long &work)
+{
+    const uint4 *M = reinterpret_cast<const uint4 *>(x.mbuf);
+    if constexpr (R == 1) {
+        if (lane == 0) {
+            uint32_t t = 0;
+#pragma unroll
+            for (int q = 0; q < CW; q++) t += __popc(C[q]);
+            acc += t;
+        }
+    } else if constexpr (R == 2 || R == 3) {
+        uint32_t s = 0;
+        cdfs_word<R, CW, TRI, WORK, 0>(M, C, lane, s, work);
+        acc += s;
+    } else {
+        // members in order; one recursive call site per level keeps the code linear in R
+        uint32_t rem[CW];
+#pragma unroll
+        for (int t = 0; t < CW; t++) rem[t] = C[t];
+        for (;;) {
+            int q = -1;
+            uint32_t word = 0;
+#pragma unroll
+            for (int t = CW - 1; t >= 0; t--)
+                if (rem[t]) {
+                    q = t;
+                    word = rem[t];
+                }
+            if (q < 0) break;
+            const uint32_t i = (uint32_t)(q << 5) + __ffs(word) - 1;
+#pragma unroll
+            for (int t = 0; t < CW; t++)
+                if (t == q) rem[t] &= rem[t] - 1;
+            const uint4 mi = M[i];
+            uint32_t C2[CW];
+            C2[0] = C[0] & mi.x;
+            if (CW > 1) C2[1] = C[1] & mi.y;
+            if (CW > 2) C2[2] = C[2] & mi.z;
+            if (CW > 3) C2[3] = C[3] & mi.w;
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int t = 0; t < CW; t++) cnt += __popc(C2[t]);
+            if (WORK && lane == 0) work += CW;
+            if (cnt >= R - 1) cdfs<R - 1, CW, TRI, WORK>(x, C2, lane, acc, work);
+        }
+    }
+}
+
+template <int R, int CW, bool TRI, bool WORK>
+__device__ __forceinline__ void cdfs_all(const WarpCtx &x, uint32_t s, int lane,
+                                         unsigned long long &acc, unsigned long long &work)
+{
+    uint32_t C[CW];
+#pragma unroll
+    for (int q = 0; q < CW; q++) {
+        const uint32_t lo = q * 32;
+        C[q] = s >= lo + 32 ? kFull : (s > lo ? ((1u << (s - lo)) - 1) : 0u);
+    }
+    cdfs<R, CW, TRI, WORK>(x, C, lane, acc, work);
+}
+
+// Entry for a candidate set of at most compact_max members (lane word c), triangular layout.
+template <int R, bool WORK>
+__device__ __forceinline__ void compact_entry(const WarpCtx &x, uint32_t c, int lane,
+                                              unsigned long long &acc, unsigned long long &work)
+{
+    int clo, chi;
+    const uint32_t s = compact(x, c, lane, clo, chi);
+    if (s <= 128) {
+        build_compact<4>(x, s, clo, chi, lane);
+        if (s <= 32) cdfs_all<R, 1, true, WORK>(x, s, lane, acc, work);
+        else if (s <= 64) cdfs_all<R, 2, true, WORK>(x, s, lane, acc, work);
+        else if (s <= 96) cdfs_all<R, 3, true, WORK>(x, s, lane, acc, work);
+        else cdfs_all<R, 4, true, WORK>(x, s, lane, acc, work);
+    }
+    __syncwarp();
+}
+
+// Counts the R-cliques inside the candidate set whose word w sits in lane w (words >= W are
+// zero); adds lane-partial sums to acc.
+//   R >= 4: warp-uniform walk over the members a; the next candidate set c ∧ row_a is again
+//           spread over the lanes (one shared-memory load per lane).
+//   R == 3: members are compacted and dealt to lanes; each lane builds its own c ∧ row_a and
+//           sums its arcs (the last two levels run lane-parallel).
+//   R == 2: members dealt to lanes, each adds |c ∧ row_a|.
+template <int R, bool WORK>
+__device__ __forceinline__ void warp_dfs(const WarpCtx &x, uint32_t c, int lane,
+                                         unsigned long long &acc, unsigned long long &work)
+{
+    if constexpr (R >= 3) {
+        if (x.tri && __reduce_add_sync(kFull, __popc(c)) <= x.compact_max) {
+            compact_entry<R, WORK>(x, c, lane, acc, work);
+            return;
+        }
+    }
+    if constexpr (R == 1) {
+        acc += __popc(c);
+    } else if constexpr (R == 2) {
+        const uint32_t nz = __ballot_sync(kFull, c != 0);
+        if (__popc(nz) <= 4) {
+            // few words: lane l takes bit l of each non-zero word in turn
+            if (lane < (int)x.W) x.cbuf[lane] = c;
+            __syncwarp();
+            const int chi = 32 - __clz(nz);
+            uint32_t outer = nz, s = 0;
+            while (outer) {
+                const int w = __ffs(outer) - 1;
+                outer &= outer - 1;
+                const uint32_t cw = x.cbuf[w];
+                if ((cw >> lane) & 1) {
+                    const uint32_t *ra = x.rows + (uint32_t)(w * 32 + lane) * x.RS;
+                    const int w0 = x.tri ? w : (__ffs(nz) - 1);
+                    if (WORK) work += (uint32_t)(chi - w0);
+                    for (int w2 = w0; w2 < chi; w2++) s += __popc(x.cbuf[w2] & ra[w2]);
+                }
+            }
+            acc += s;
+            __syncwarp();
+        } else if (x.tri) {
+            int clo, chi;
+            const uint32_t total = compact(x, c, lane, clo, chi);
+            acc += tri_rounds<false, WORK>(x, x.cbuf, 0, total, chi, lane, work);
+            __syncwarp();
+        } else {
+            int clo, chi;
+            const uint32_t total = compact(x, c, lane, clo, chi);
+            uint32_t s = 0;
+            for (uint32_t i = lane; i < total; i += 32) {
+                const uint32_t a = x.elem[i];
+                const uint32_t *ra = x.rows + a * x.RS;
+                const int w0 = x.tri ? (int)(a >> 5) : clo;
+                if (WORK) work += (uint32_t)(chi - w0);
+                for (int w = w0; w < chi; w++) s += __popc(x.cbuf[w] & ra[w]);
+            }
+            acc += s;
+            __syncwarp();
+        }
+    } else if constexpr (R == 3) {
+        int clo, chi;
+        const uint32_t total = compact(x, c, lane, clo, chi);
+        uint32_t *lb = x.lbuf + lane;
+        for (uint32_t i = lane; i < total; i += 32) {
+            const uint32_t a = x.elem[i];
+            const uint32_t *ra = x.rows + a * x.RS;
+            uint32_t cnt = 0;
+            int nlo = 32, nhi = 0;
+            const int w0 = x.tri ? (int)(a >> 5) : clo;
+            if (WORK) work += (uint32_t)(chi - w0);
+            for (int w = w0; w < chi; w++) {
+                const uint32_t v = x.cbuf[w] & ra[w];
+                lb[w * 32] = v;
+                if (v) {
+                    cnt += __popc(v);
+                    nlo = min(nlo, w);
+                    nhi = w + 1;
+                }
+            }
+            if (cnt >= 2) acc += lane_arcs<WORK>(x, lb, nlo, nhi, work);
+        }
+        __syncwarp();
+    } else {
+        uint32_t rem = c;
+        for (;;) {
+            const uint32_t nz = __ballot_sync(kFull, rem != 0);
+            if (!nz) break;
+            const int wl = __ffs(nz) - 1;
+            const uint32_t word = __shfl_sync(kFull, rem, wl);
+            const uint32_t a = wl * 32 + __ffs(word) - 1;
+            if (lane == wl) rem &= rem - 1;
+            const uint32_t c2 = lane < (int)x.W ? (c & x.rows[a * x.RS + lane]) : 0u;
+            if (WORK && lane < (int)x.W) work += 1;
+            const uint32_t cnt = __reduce_add_sync(kFull, __popc(c2));
+            if (cnt >= R - 1) warp_dfs<R - 1, WORK>(x, c2, lane, acc, work);
+        }
+    }
+}
+
+// Shared-memory words one warp needs for roots of out-degree <= dcap (dcap multiple of 32).
+// Layout: elem (dcap uint16) | cbuf (32) | compress masks + prefixes (192) | lbuf/mbuf, where
+// mbuf holds compact_max rows of 4 words.
+__host__ __device__ __forceinline__ uint32_t warp_scratch_words(uint32_t dcap, uint32_t compact_max)
+{
+    const uint32_t m = compact_max * 4;
+    return dcap / 2 + 32 + 192 + (dcap > m ? dcap : m);
+}
+
+constexpr int kMidMaxWarps = 32;
+
+template <int K, bool WORK>
+__global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
+    const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
+    const uint32_t *__restrict__ list, const CountStats *st, uint32_t *next, uint32_t dcap,
+    uint32_t compact_max, unsigned long long *result, unsigned long long *per_root,
+    unsigned long long *work_out, uint32_t *err)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const uint32_t rs_cap = (dcap / 32) | 1;
+    uint32_t *sL = smem;
+    uint32_t *rows = smem + dcap;
+    __shared__ uint32_t s_idx, s_task, s_tri;
+    __shared__ unsigned long long s_acc[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t *wscr = rows + (size_t)dcap * rs_cap + (size_t)w * warp_scratch_words(dcap, compact_max);
+    WarpCtx x;
+    x.rows = rows;
+    x.elem = reinterpret_cast<uint16_t *>(wscr);
+    x.cbuf = wscr + dcap / 2;
+    x.mv = wscr + dcap / 2 + 32;
+    x.lbuf = wscr + dcap / 2 + 32 + 192;
+    x.mbuf = x.lbuf;
+    x.compact_max = compact_max;
+    const uint32_t nlist = st->n_mid;
+    unsigned long long block_total = 0;  // meaningful in thread 0
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_idx = atomicAdd(next, 1u);
+            s_task = 0;
+            s_tri = 1;
+        }
+        __syncthreads();
+        const uint32_t idx = s_idx;
+        if (idx >= nlist) break;
+        const uint32_t u = list[idx];
+        const uint64_t base = dag_off[u];
+        const uint32_t D = (uint32_t)(dag_off[u + 1] - base);
+        const uint32_t W = (D + 31) >> 5, RS = W | 1;
+        for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) sL[i] = dag_cols[base + i];
+        if (K > 3)
+            for (uint32_t i = threadIdx.x; i < D * RS; i += blockDim.x) rows[i] = 0;
+        __syncthreads();
+        const uint32_t lmax = sL[D - 1];
+        unsigned long long acc = 0, work = 0;
+        // Build the local subgraph: row i = V(g_u) ∩ N+(a_i) (CITRON's GenSubgraph).  Each step
+        // loads 64 entries of N+(a_i) (two per lane) so that two loads are in flight.
+        bool tri = true;
+        for (uint32_t i = w; i < D; i += nw) {
+            const uint32_t a = sL[i];
+            const uint64_t b = dag_off[a], e = dag_off[a + 1];
+            for (uint64_t p = b; p < e; p += 64) {
+                const uint32_t y0 = p + lane < e ? dag_cols[p + lane] : 0xffffffffu;
+                const uint32_t y1 = p + 32 + lane < e ? dag_cols[p + 32 + lane] : 0xffffffffu;
+                if (__shfl_sync(kFull, y0, 0) > lmax) break;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t y = h ? y1 : y0;
+                    if (y <= lmax) {
+                        const uint32_t j = lower_bound_smem(sL, D, y);
+                        if (sL[j] == y) {
+                            if (K == 3) {
+                                acc += 1;
+                            } else {
+                                atomicOr(&rows[i * RS + (j >> 5)], 1u << (j & 31));
+                                tri &= j > i;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (K > 3) {
+            if (!__all_sync(kFull, tri) && lane == 0) s_tri = 0;
+            __syncthreads();
+            x.RS = RS;
+            x.W = W;
+            x.tri = s_tri != 0;
+            // Edge tasks (u, a_t): count (K-2)-cliques in row t.
+            for (;;) {
+                uint32_t t = 0;
+                if (lane == 0) t = atomicAdd(&s_task, 1u);
+                t = __shfl_sync(kFull, t, 0);
+                if (t >= D) break;
+                const uint32_t c = lane < W ? rows[t * RS + lane] : 0u;
+                const uint32_t cnt = __reduce_add_sync(kFull, __popc(c));
+                if (cnt >= K - 2) warp_dfs<K - 2, WORK>(x, c, lane, acc, work);
+            }
+        }
+        if (WORK) {
+            const unsigned long long wsum = warp_sum_u64(work, err);
+            if (lane == 0 && wsum) atomicAdd(work_out, wsum);
+        }
+        const unsigned long long ws = warp_sum_u64(acc, err);
+        if (lane == 0) s_acc[w] = ws;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long r = 0;
+            bool wrapped = false;
+            for (int i = 0; i < nw; i++) {
+                const unsigned long long s2 = r + s_acc[i];
+                wrapped |= s2 < r;
+                r = s2;
+            }
+            if (wrapped) set_error(err, kDevOverflow);
+            if (per_root) per_root[u] = r;
+            const unsigned long long s2 = block_total + r;
+            if (s2 < block_total) set_error(err, kDevOverflow);
+            block_total = s2;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) add_checked(result, block_total, err);
+}
+
+// ------------------------------------------------------------------------------------------
+// Sorted-list path (D > bitmap_max).
+
+// R-cliques inside the sorted candidate list C[0..len); buf holds one list per deeper level.
+template <int R>
+__device__ void list_dfs(const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ cols,
+                         const uint32_t *C, uint32_t len, uint32_t *buf, uint32_t stride, int lane,
+                         unsigned long long &acc)
+{
+    if (len < (uint32_t)R) return;
+    if constexpr (R == 1) {
+        if (lane == 0) acc += len;
+    } else {
+        for (uint32_t i = 0; i < len; i++) {
+            const uint32_t a = C[i];
+            const uint64_t ab = dag_off[a], ae = dag_off[a + 1];
+            uint32_t out = 0;
+            for (uint32_t p = 0; p < len; p += 32) {
+                bool hit = false;
+                uint32_t x = 0;
+                if (p + lane < len) {
+                    x = C[p + lane];
+                    uint64_t lo = ab, hi = ae;
+                    while (lo < hi) {
+                        const uint64_t mid = lo + (hi - lo) / 2;
+                        if (cols[mid] < x) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    hit = lo < ae && cols[lo] == x;
+                }
+                const uint32_t bal = __ballot_sync(kFull, hit);
+                if constexpr (R == 2) {
+                    if (lane == 0) acc += __popc(bal);
+                } else {
+                    if (hit) buf[out + __popc(bal & lanemask_lt())] = x;
+                }
+                out += __popc(bal);
+            }
+            if constexpr (R >= 3) {
+                __syncwarp();
+                if (out >= (uint32_t)(R - 1))
+                    list_dfs<R - 1>(dag_off, cols, buf, out, buf + stride, stride, lane, acc);
+                __syncwarp();
+            }
+        }
+    }
+}
+
+template <int K>
+__global__ __launch_bounds__(kListWarps * 32) void k_count_list(
+    const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
+    const uint32_t *__restrict__ list, const CountStats *st, uint32_t *next, uint32_t *scratch,
+    uint32_t stride, unsigned long long *result, unsigned long long *per_root, uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = blockIdx.x * kListWarps + (threadIdx.x >> 5);
+    uint32_t *buf = scratch + (size_t)gw * stride * (K > 3 ? K - 3 : 1);
+    const uint32_t nlist = st->n_big;
+    unsigned long long total = 0;
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(next, 1u);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= nlist) break;
+        const uint32_t u = list[idx];
+        const uint64_t base = dag_off[u];
+        const uint32_t D = (uint32_t)(dag_off[u + 1] - base);
+        if (D > stride) {
+            if (lane == 0) set_error(err, kDevScratch);
+            continue;
+        }
+        unsigned long long acc = 0;
+        list_dfs<K - 1>(dag_off, dag_cols, dag_cols + base, D, buf, stride, lane, acc);
+        if (per_root) {
+            const unsigned long long r = warp_sum_u64(acc, err);
+            if (lane == 0) per_root[u] = r;
+        }
+        total += acc;
+    }
+    total = warp_sum_u64(total, err);
+    if (lane == 0) add_checked(result, total, err);
+}
+
+}  // namespace citron
+
+namespace citron_host {
+using namespace citron;
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool on;
+    cudaStream_t s;
+    Timer(bool enable, cudaStream_t st) : on(enable), s(st)
+    {
+        if (on && (cudaEventCreate(&a) || cudaEventCreate(&b))) on = false;
+        if (on) cudaEventRecord(a, s);
+    }
+    void stop() { if (on) cudaEventRecord(b, s); }
+    float ms()
+    {
+        float t = 0;
+        if (on && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&t, a, b);
+        return t;
+    }
+    ~Timer()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+template <int K, bool WORK>
+static cudaError_t launch_mid(uint32_t grid_cap, uint32_t dcap, uint32_t compact_max, uint32_t warps,
+                              size_t smem,
+                              const uint64_t *dag_off, const uint32_t *dag_cols,
+                              const uint32_t *mid_list, const CountStats *st, uint32_t *next,
+                              unsigned long long *result, unsigned long long *per_root,
+                              unsigned long long *work, uint32_t *err, cudaStream_t s, int num_sms)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_count_mid<K, WORK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_mid<K, WORK>, warps * 32,
+                                                           smem)))
+        return e;
+    if (per_sm < 1) per_sm = 1;
+    uint32_t grid = (uint32_t)(num_sms * per_sm);
+    if (grid > grid_cap) grid = grid_cap;
+    k_count_mid<K, WORK><<<grid, warps * 32, smem, s>>>(dag_off, dag_cols, mid_list, st, next, dcap,
+                                                        compact_max, result, per_root, work, err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const uint32_t *dag_cols,
+                                  const CountStats &hs, const CountStats *st,
+                                  const uint32_t *small_list, const uint32_t *mid_list,
+                                  const uint32_t *big_list, uint32_t *next, uint32_t *list_scratch,
+                                  size_t list_scratch_words, unsigned long long *result,
+                                  unsigned long long *work, uint32_t *err, cudaStream_t s,
+                                  int num_sms)
+{
+    cudaError_t e = cudaSuccess;
+    const CountPlan &plan = run.plan;
+    if (hs.n_mid) {
+        const uint32_t dcap = (hs.max_mid + 31) & ~31u;
+        const uint32_t rs = (dcap / 32) | 1;
+        int smem_cap = 0, dev = 0;
+        cudaGetDevice(&dev);
+        if ((e = cudaDeviceGetAttribute(&smem_cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)))
+            return e;
+        smem_cap -= 1024;  // static shared memory of the kernel
+        auto smem_for = [&](uint32_t warps) {
+            return ((size_t)dcap +
+                    (K > 3 ? (size_t)dcap * rs + (size_t)warps * warp_scratch_words(dcap, plan.compact_max) : 0)) *
+                   sizeof(uint32_t);
+        };
+        uint32_t warps = plan.warps_per_cta > (uint32_t)kMidMaxWarps ? kMidMaxWarps : plan.warps_per_cta;
+        while (warps > 1 && smem_for(warps) > (size_t)smem_cap) warps--;
+        Timer t(run.time_kernels, s);
+        if (run.count_work)
+            e = launch_mid<K, true>(hs.n_mid, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
+                                    mid_list, st, next + 0, result, run.per_root, work, err, s,
+                                    num_sms);
+        else
+            e = launch_mid<K, false>(hs.n_mid, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
+                                     mid_list, st, next + 0, result, run.per_root, work, err, s,
+                                     num_sms);
+        if (e) return e;
+        t.stop();
+        run.kernel_ms[1] = t.ms();
+    }
+    if (hs.n_small) {
+        uint32_t grid = (hs.n_small + kSmallWarps - 1) / kSmallWarps;
+        const uint32_t cap = (uint32_t)num_sms * 16;
+        if (grid > cap) grid = cap;
+        Timer t(run.time_kernels, s);
+        k_count_small<K><<<grid, kSmallWarps * 32, 0, s>>>(dag_off, dag_cols, small_list, st, result,
+                                                           run.per_root, err);
+        note_launches(1);
+        if ((e = cudaGetLastError())) return e;
+        t.stop();
+        run.kernel_ms[0] = t.ms();
+    }
+    if (hs.n_big) {
+        const size_t per_warp = (size_t)hs.max_big * (K > 3 ? K - 3 : 1);
+        size_t warps = per_warp ? list_scratch_words / per_warp : 0;
+        if (warps < kListWarps) return cudaErrorMemoryAllocation;
+        uint32_t grid = (uint32_t)(warps / kListWarps);
+        const uint32_t cap = (uint32_t)num_sms;
+        if (grid > cap) grid = cap;
+        if (grid > (hs.n_big + kListWarps - 1) / kListWarps) grid = (hs.n_big + kListWarps - 1) / kListWarps;
+        Timer t(run.time_kernels, s);
+        k_count_list<K><<<grid, kListWarps * 32, 0, s>>>(dag_off, dag_cols, big_list, st, next + 1,
+                                                         list_scratch, hs.max_big, result,
+                                                         run.per_root, err);
+        note_launches(1);
+        if ((e = cudaGetLastError())) return e;
+        t.stop();
+        run.kernel_ms[2] = t.ms();
+    }
+    return cudaSuccess;
+}
+
+// Per-k launchers, each compiled in its own translation unit (count_k*.cu).
+#define CITRON_LAUNCH_K_DECL(KK)                                                                     \
+    cudaError_t launch_count_##KK(CountRun &run, const uint64_t *dag_off, const uint32_t *dag_cols,  \
+                                  const CountStats &hs, const CountStats *st,                       \
+                                  const uint32_t *small_list, const uint32_t *mid_list,             \
+                                  const uint32_t *big_list, uint32_t *next, uint32_t *list_scratch, \
+                                  size_t list_scratch_words, unsigned long long *result,            \
+                                  unsigned long long *work, uint32_t *err, cudaStream_t s,          \
+                                  int num_sms)
+#define CITRON_LAUNCH_K_DEF(KK)                                                                      \
+    CITRON_LAUNCH_K_DECL(KK)                                                                         \
+    {                                                                                                \
+        return launch_count_k<KK>(run, dag_off, dag_cols, hs, st, small_list, mid_list, big_list,   \
+                                  next, list_scratch, list_scratch_words, result, work, err, s,     \
+                                  num_sms);                                                         \
+    }
+CITRON_LAUNCH_K_DECL(3);
+CITRON_LAUNCH_K_DECL(4);
+CITRON_LAUNCH_K_DECL(5);
+CITRON_LAUNCH_K_DECL(6);
+CITRON_LAUNCH_K_DECL(7);
+CITRON_LAUNCH_K_DECL(8);
+CITRON_LAUNCH_K_DECL(9);
+CITRON_LAUNCH_K_DECL(10);
+CITRON_LAUNCH_K_DECL(11);
+CITRON_LAUNCH_K_DECL(12);
+
+}  // namespace citron_host

@@ -4,13 +4,14 @@
 //     k_radix_hist / k_radix_scatter: stable LSD radix sort of the ids by degree, 8-bit digits;
 //     ids enter in ascending order, so stability supplies the id tie-break.
 //   Algorithm GenOrdering (Sec. IV), fused into ONE pass over the arcs:
-//     k_tile_rows     : for every tile of 4096 arcs, the first vertex whose row starts in it;
-//     k_gen_ordering  : keep-test of every arc, block scan, decoupled look-back prefix over tiles,
-//                       coalesced store of the kept arcs (the DAG columns, already sorted per
-//                       row) and of the DAG row offsets.  The count pass, PrefixSum and the fill
-//                       pass of the listing become one read of cols and one write of the DAG.
+//     k_tile_rows       : for every tile of 4096 arcs, the first vertex whose row starts in it;
+//     k_dag_compact<0>  : keep-test of every arc, block scan, decoupled look-back prefix over
+//                         tiles, coalesced store of the kept arcs (the DAG columns, already sorted
+//                         per row) and of the DAG row offsets.  The count pass, PrefixSum and the
+//                         fill pass of the listing become one read of cols and one write of the DAG.
 //   Relabelled DAG from any rank (Sec. II directionalizing, rows renamed to ranks):
-//     k_outdeg_rank -> k_scan_rowlen (look-back) -> k_fill_rank (+ k_fill_rank_long).
+//     k_dag_compact<1> (kept ranks, input row order) -> k_rl_rowlen -> k_scan_rowlen (look-back)
+//     -> k_rl_sort (per-row sort into rank order; k_rl_sort_long for rows above 1024).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -51,20 +52,35 @@ __global__ __launch_bounds__(kRsThreads) void k_radix_hist(const uint64_t *off, 
     hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Exclusive scan of one uint32 array by a single block (sizes here are 256 x blocks).
+// Exclusive scan of one uint32 array by a single block of 1024 threads (sizes here are
+// 256 x blocks).  Each warp owns one contiguous segment and walks it 32 entries at a time, so
+// every load and store is coalesced.
 __global__ __launch_bounds__(1024) void k_scan_small(uint32_t *data, uint32_t count)
 {
-    __shared__ uint32_t scratch[33];
-    const uint32_t per = (count + blockDim.x - 1) / blockDim.x;
-    const uint32_t lo = min(count, threadIdx.x * per), hi = min(count, lo + per);
-    uint32_t s = 0;
-    for (uint32_t i = lo; i < hi; i++) s += data[i];
-    uint32_t total;
-    uint32_t run = block_excl_scan(s, scratch, total);
-    for (uint32_t i = lo; i < hi; i++) {
-        uint32_t v = data[i];
-        data[i] = run;
-        run += v;
+    __shared__ uint32_t s_warp[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t seg = ((count + 31) / 32 + 31) & ~31u;
+    const uint32_t lo = min(count, (uint32_t)w * seg), hi = min(count, lo + seg);
+    uint32_t sum = 0;
+#pragma unroll 4
+    for (uint32_t i = lo + lane; i < hi; i += 32) sum += data[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    if (lane == 0) s_warp[w] = sum;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t v = s_warp[lane];
+        const uint32_t incl = warp_incl_scan(v);
+        s_warp[lane] = incl - v;
+    }
+    __syncthreads();
+    uint32_t carry = s_warp[w];
+    for (uint32_t i0 = lo; i0 < hi; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const uint32_t v = i < hi ? data[i] : 0u;
+        const uint32_t incl = warp_incl_scan(v);
+        if (i < hi) data[i] = carry + incl - v;
+        carry += __shfl_sync(kFull, incl, 31);
     }
 }
 
@@ -143,18 +159,29 @@ __global__ void k_tile_rows(uint32_t n, uint64_t arcs, const uint64_t *off, uint
     if (owns_end) first_row[ntiles] = (uint32_t)u;
 }
 
-__device__ __forceinline__ bool degree_before(uint64_t du, uint32_t u, uint64_t dv, uint32_t v)
+// deg[u] = off[u+1] - off[u] (clamped to 32 bits): the key of the degree ordering.
+__global__ void k_degrees(uint32_t n, const uint64_t *__restrict__ off, uint32_t *__restrict__ deg)
 {
-    return du < dv || (du == dv && u < v);
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) deg[u] = (uint32_t)min(off[u + 1] - off[u], (uint64_t)0xffffffffull);
 }
 
-__global__ __launch_bounds__(kGoThreads) void k_gen_ordering(
+// One pass over the arcs in tiles of 4096: keep-test of every arc, block scan, decoupled look-back
+// prefix over tiles, coalesced store of the kept values and of the row offsets.
+//   ORDER = 0 (Algorithm GenOrdering, Sec. IV): key = degree; u -> v kept iff
+//             (d(u), u) < (d(v), v); the kept value is v.  Rows keep the input's order.
+//   ORDER = 1 (any rank): key = rank; kept iff rank[v] > rank[u]; the kept value is rank[v]
+//             (rows stay in input order, unsorted: the relabel pass sorts them).
+// Every thread issues the key gathers of its 16 arcs before it uses any of them.
+template <int ORDER>
+__global__ __launch_bounds__(kGoThreads) void k_dag_compact(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ cols,
-    const uint32_t *__restrict__ first_row, uint32_t ntiles, uint64_t *__restrict__ dag_off,
-    uint32_t *__restrict__ dag_cols, uint64_t dag_cap, unsigned long long *status,
-    uint32_t *ticket, uint32_t *err, int vec4)
+    const uint32_t *__restrict__ key, const uint32_t *__restrict__ first_row, uint32_t ntiles,
+    uint64_t *__restrict__ out_off, uint32_t *__restrict__ out_vals, uint64_t out_cap,
+    unsigned long long *status, uint32_t *ticket, uint32_t *err, int vec4)
 {
     __shared__ uint64_t s_row[kGoRowCap + 1];
+    __shared__ uint32_t s_key[kGoRowCap + 1];
     __shared__ uint32_t s_out[kGoTile];
     __shared__ uint32_t s_pref[kGoThreads];
     __shared__ uint16_t s_mask[kGoThreads];
@@ -179,26 +206,20 @@ __global__ __launch_bounds__(kGoThreads) void k_gen_ordering(
     const uint32_t nrows = bad ? 0 : u_next - r0;  // rows r0 .. u_next-1 may hold arcs of this tile
     const bool cached = nrows + 1 <= kGoRowCap + 1;
     if (bad && tid == 0) set_error(err, kDevBadInput);
-    if (cached)
-        for (uint32_t i = tid; i <= nrows; i += kGoThreads) s_row[i] = off[r0 + i];
+    if (cached) {
+        for (uint32_t i = tid; i <= nrows; i += kGoThreads) {
+            s_row[i] = off[r0 + i];
+            s_key[i] = (r0 + i < n) ? key[r0 + i] : 0u;
+        }
+    }
     __syncthreads();
     auto row_start = [&](uint32_t r) -> uint64_t {  // off[r] for r in [r0, u_next]
         return cached ? s_row[r - r0] : off[r];
     };
+    auto row_key = [&](uint32_t r) -> uint32_t { return cached ? s_key[r - r0] : key[r]; };
 
-    // Rows of this thread's first arc: last r in [r0, u_next] with off[r] <= a.
     const uint64_t a0 = bad ? t1 : t0 + (uint64_t)tid * kGoItems;
-    uint32_t r = r0;
-    if (a0 < t1) {
-        uint32_t lo = r0, hi = u_next;  // invariant off[lo] <= a0
-        while (lo < hi) {
-            uint32_t mid = lo + (hi - lo + 1) / 2;
-            if (row_start(mid) <= a0) lo = mid;
-            else hi = mid - 1;
-        }
-        r = lo;
-    }
-    uint32_t v[kGoItems];
+    uint32_t v[kGoItems], kv[kGoItems];
     if (vec4 && a0 + kGoItems <= t1) {
         const uint4 *p = reinterpret_cast<const uint4 *>(cols + a0);
 #pragma unroll
@@ -213,26 +234,40 @@ __global__ __launch_bounds__(kGoThreads) void k_gen_ordering(
 #pragma unroll
         for (int j = 0; j < kGoItems; j++) v[j] = (a0 + j < t1) ? cols[a0 + j] : 0;
     }
+    // all key gathers in flight before any is used
+#pragma unroll
+    for (int j = 0; j < kGoItems; j++) kv[j] = (a0 + j < t1 && v[j] < n) ? __ldg(key + v[j]) : 0u;
+    // row of this thread's first arc: last r in [r0, u_next] with off[r] <= a0
+    uint32_t r = r0;
+    if (a0 < t1) {
+        uint32_t lo = r0, hi = u_next;  // invariant off[lo] <= a0
+        while (lo < hi) {
+            uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (row_start(mid) <= a0) lo = mid;
+            else hi = mid - 1;
+        }
+        r = lo;
+    }
     uint32_t mask = 0;
     if (a0 < t1) {
-        uint64_t rs = row_start(r), re = row_start(r + 1);
+        uint64_t re = row_start(r + 1);
+        uint32_t ku = row_key(r);
 #pragma unroll
         for (int j = 0; j < kGoItems; j++) {
             const uint64_t a = a0 + j;
             if (a < t1) {
                 while (re <= a) {
                     r++;
-                    rs = re;
                     re = row_start(r + 1);
+                    ku = row_key(r);
                 }
                 const uint32_t w = v[j];
                 if (w >= n) {
                     set_error(err, kDevBadInput);
                     continue;
                 }
-                const uint64_t du = re - rs;
-                const uint64_t dw = __ldg(off + w + 1) - __ldg(off + w);
-                if (degree_before(du, r, dw, w)) mask |= 1u << j;
+                const bool keep = ORDER == 0 ? (ku < kv[j] || (ku == kv[j] && r < w)) : (kv[j] > ku);
+                if (keep) mask |= 1u << j;
             }
         }
     }
@@ -244,7 +279,7 @@ __global__ __launch_bounds__(kGoThreads) void k_gen_ordering(
         uint32_t p = pref;
 #pragma unroll
         for (int j = 0; j < kGoItems; j++)
-            if (mask >> j & 1) s_out[p++] = v[j];
+            if (mask >> j & 1) s_out[p++] = ORDER == 0 ? v[j] : kv[j];
     }
     if (tid < 32) {
         unsigned long long e = lookback_warp(status, t, total, err);
@@ -252,53 +287,42 @@ __global__ __launch_bounds__(kGoThreads) void k_gen_ordering(
     }
     __syncthreads();
     const unsigned long long excl = s_excl;
-    if (excl + total > dag_cap) {  // more kept arcs than half the input: asymmetric input
+    if (excl + total > out_cap) {  // more kept arcs than half the input: asymmetric input
         if (tid == 0) set_error(err, kDevBadInput);
         return;
     }
-    for (uint32_t i = tid; i < total; i += kGoThreads) dag_cols[excl + i] = s_out[i];
+    for (uint32_t i = tid; i < total; i += kGoThreads) out_vals[excl + i] = s_out[i];
     if (bad) return;
-    // DAG row offsets of the vertices whose rows start inside this tile.
+    // row offsets of the vertices whose rows start inside this tile
     for (uint32_t u = u_first + tid; u < u_next; u += kGoThreads) {
         const uint32_t pos = (uint32_t)(row_start(u) - t0);
         const uint32_t q = pos / kGoItems, j = pos % kGoItems;
-        dag_off[u] = excl + s_pref[q] + __popc((uint32_t)s_mask[q] & ((1u << j) - 1));
+        out_off[u] = excl + s_pref[q] + __popc((uint32_t)s_mask[q] & ((1u << j) - 1));
     }
     if (t == ntiles - 1) {  // trailing vertices whose rows start at the end of the arcs
-        for (uint32_t u = first_row[ntiles] + tid; u <= n; u += kGoThreads) dag_off[u] = excl + total;
+        for (uint32_t u = first_row[ntiles] + tid; u <= n; u += kGoThreads) out_off[u] = excl + total;
     }
 }
 
 // ------------------------------------------------------------------------------------------
 // Relabelled DAG from a rank permutation.
 
-// rowlen[rank[u]] = #{v in N(u) : rank[v] > rank[u]}; warp per vertex.
-__global__ void k_outdeg_rank(uint32_t n, const uint64_t *__restrict__ off,
-                              const uint32_t *__restrict__ cols, const uint32_t *__restrict__ rank,
-                              uint32_t *__restrict__ rowlen, uint32_t *max_len, uint32_t *err)
+// rowlen[rank[u]] = length of u's kept row (G[u+1] - G[u]); the largest goes to max_len.
+__global__ void k_rl_rowlen(uint32_t n, const uint64_t *__restrict__ G,
+                            const uint32_t *__restrict__ rank, uint32_t *__restrict__ rowlen,
+                            uint32_t *max_len, uint32_t *err)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-    uint32_t best = 0;
-    for (uint32_t u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
-        const uint64_t b = off[u], e = off[u + 1];
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t len = 0;
+    if (u < n) {
         const uint32_t ru = rank[u];
-        if (ru >= n) {
-            if (lane == 0) set_error(err, kDevBadInput);
-            continue;
-        }
-        uint32_t c = 0;
-        for (uint64_t i = b + lane; i < e; i += 32) {
-            const uint32_t v = cols[i];
-            if (v < n) c += rank[v] > ru;
-            else set_error(err, kDevBadInput);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-        if (lane == 0) rowlen[ru] = c;
-        best = max(best, c);
+        len = (uint32_t)min(G[u + 1] - G[u], (uint64_t)0xffffffffull);
+        if (ru < n) rowlen[ru] = len;
+        else set_error(err, kDevBadInput);
     }
-    if (lane == 0 && best) atomicMax(max_len, best);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(kFull, len, o));
+    if ((threadIdx.x & 31) == 0 && len) atomicMax(max_len, len);
 }
 
 constexpr int kScThreads = 256;
@@ -367,114 +391,107 @@ __device__ __forceinline__ void bitonic_smem(uint32_t *s, uint32_t p, int lane, 
     }
 }
 
-constexpr int kFrWarps = 8;
-constexpr uint32_t kFrCap = 1024;  // rows up to this length are sorted by one warp
-
-// Fill row rank[u] with the ranks of u's later neighbours, sorted.  Warp per vertex; longer
-// rows are listed for k_fill_rank_long.
-__global__ __launch_bounds__(kFrWarps * 32) void k_fill_rank(
-    uint32_t n, const uint64_t *__restrict__ off, const uint32_t *__restrict__ cols,
-    const uint32_t *__restrict__ rank, const uint64_t *__restrict__ dag_off,
-    uint32_t *__restrict__ dag_cols, uint32_t *long_rows, uint32_t *n_long)
+// Ascending bitonic sort of one value per lane (32 values) with shuffles.
+__device__ __forceinline__ uint32_t bitonic_warp(uint32_t x, int lane)
 {
-    __shared__ uint32_t s_buf[kFrWarps][kFrCap];
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t y = __shfl_xor_sync(kFull, x, j);
+            const bool up = (lane & k) == 0;
+            const bool lower = (lane & j) == 0;
+            x = (lower == up) ? min(x, y) : max(x, y);
+        }
+    }
+    return x;
+}
+
+constexpr int kRlWarps = 8;
+constexpr uint32_t kRlRows = 256;     // rows staged per block step
+constexpr uint32_t kRlWarpCap = 1024; // rows up to this length are sorted by one warp
+constexpr uint32_t kLongCap = 32768;  // longest relabelled row this build sorts (power of 2)
+
+// Relabel: kept row of input vertex u (values = ranks, input order) goes to row rank[u] of the
+// DAG, sorted.  Blocks take 256 consecutive input rows at a time; the rows' offsets, ranks and
+// destinations are staged in shared memory first (coalesced and independent loads), then each
+// warp sorts whole rows (shuffles up to 32 entries, shared memory up to 1024).  Longer rows are
+// listed for k_rl_sort_long.
+__global__ __launch_bounds__(kRlWarps * 32) void k_rl_sort(
+    uint32_t n, const uint64_t *__restrict__ G, const uint32_t *__restrict__ vals,
+    const uint32_t *__restrict__ rank, const uint64_t *__restrict__ dag_off,
+    uint32_t *__restrict__ dag_cols, uint64_t dag_cap, uint32_t *long_rows, uint32_t *n_long,
+    uint32_t *err)
+{
+    __shared__ uint64_t s_g[kRlRows + 1];
+    __shared__ uint64_t s_dst[kRlRows];
+    __shared__ uint32_t s_buf[kRlWarps][kRlWarpCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t *buf = s_buf[w];
-    const uint32_t warps = gridDim.x * kFrWarps;
-    for (uint32_t u = blockIdx.x * kFrWarps + w; u < n; u += warps) {
-        const uint32_t ru = rank[u];
-        if (ru >= n) continue;
-        const uint64_t ob = dag_off[ru];
-        const uint32_t len = (uint32_t)(dag_off[ru + 1] - ob);
-        if (len == 0) continue;
-        if (len > kFrCap) {
-            if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = u;
-            continue;
+    for (uint32_t r0 = blockIdx.x * kRlRows; r0 < n; r0 += gridDim.x * kRlRows) {
+        const uint32_t cnt = min(kRlRows, n - r0);
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i <= cnt; i += blockDim.x) s_g[i] = G[r0 + i];
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t ru = rank[r0 + i];
+            s_dst[i] = ru < n ? dag_off[ru] : ~0ull;
         }
-        const uint64_t b = off[u], e = off[u + 1];
-        uint32_t fill = 0;
-        for (uint64_t i = b; i < e; i += 32) {
-            uint32_t x = 0;
-            bool keep = false;
-            if (i + lane < e && cols[i + lane] < n) {
-                x = rank[cols[i + lane]];
-                keep = x > ru;
+        __syncthreads();
+        for (uint32_t i = w; i < cnt; i += kRlWarps) {
+            const uint64_t b = s_g[i];
+            const uint32_t len = (uint32_t)(s_g[i + 1] - b);
+            const uint64_t dst = s_dst[i];
+            if (len == 0) continue;
+            if (dst == ~0ull || dst + len > dag_cap) {  // rank is not a permutation
+                if (lane == 0) set_error(err, kDevBadInput);
+                continue;
             }
-            const uint32_t bal = __ballot_sync(kFull, keep);
-            const uint32_t pos = fill + __popc(bal & lanemask_lt());
-            if (keep && pos < len) buf[pos] = x;
-            fill += __popc(bal);
-        }
-        if (len <= 32) {
-            // one element per lane; bitonic network over shuffles
-            uint32_t x = lane < len ? buf[lane] : 0xffffffffu;
-#pragma unroll
-            for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    const uint32_t y = __shfl_xor_sync(kFull, x, j);
-                    const bool up = (lane & k) == 0;
-                    const bool lower = (lane & j) == 0;
-                    x = (lower == up) ? min(x, y) : max(x, y);
-                }
+            if (len <= 32) {
+                uint32_t x = lane < len ? vals[b + lane] : 0xffffffffu;
+                x = bitonic_warp(x, lane);
+                if (lane < len) dag_cols[dst + lane] = x;
+            } else if (len <= kRlWarpCap) {
+                uint32_t *buf = s_buf[w];
+                uint32_t p = 64;
+                while (p < len) p <<= 1;
+                for (uint32_t j = lane; j < p; j += 32) buf[j] = j < len ? vals[b + j] : 0xffffffffu;
+                __syncwarp();
+                bitonic_smem(buf, p, lane, 32, false);
+                for (uint32_t j = lane; j < len; j += 32) dag_cols[dst + j] = buf[j];
+                __syncwarp();
+            } else if (lane == 0) {
+                long_rows[atomicAdd(n_long, 1u)] = r0 + i;
             }
-            if (lane < len) dag_cols[ob + lane] = x;
-        } else {
-            uint32_t p = 64;
-            while (p < len) p <<= 1;
-            for (uint32_t i = len + lane; i < p; i += 32) buf[i] = 0xffffffffu;
-            __syncwarp();
-            bitonic_smem(buf, p, lane, 32, false);
-            for (uint32_t i = lane; i < len; i += 32) dag_cols[ob + i] = buf[i];
         }
-        __syncwarp();
     }
 }
 
-constexpr uint32_t kLongCap = 32768;  // longest relabelled row this build sorts (power of 2)
-
 // One block per long row; dynamic shared memory holds the padded row.
-__global__ __launch_bounds__(1024) void k_fill_rank_long(
-    uint32_t n, const uint64_t *__restrict__ off, const uint32_t *__restrict__ cols,
+__global__ __launch_bounds__(1024) void k_rl_sort_long(
+    uint32_t n, const uint64_t *__restrict__ G, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ rank, const uint64_t *__restrict__ dag_off,
-    uint32_t *__restrict__ dag_cols, const uint32_t *long_rows, const uint32_t *n_long,
-    uint32_t cap, uint32_t *err)
+    uint32_t *__restrict__ dag_cols, uint64_t dag_cap, const uint32_t *long_rows,
+    const uint32_t *n_long, uint32_t cap, uint32_t *err)
 {
     extern __shared__ uint32_t s_row[];
-    __shared__ uint32_t s_fill;
-    __shared__ uint32_t s_scan[33];
     for (uint32_t it = blockIdx.x; it < *n_long; it += gridDim.x) {
         const uint32_t u = long_rows[it];
         const uint32_t ru = rank[u];
-        const uint64_t ob = dag_off[ru];
-        const uint32_t len = (uint32_t)(dag_off[ru + 1] - ob);
-        if (len > cap) {
-            if (threadIdx.x == 0) set_error(err, kDevTooLong);
+        const uint64_t b = G[u];
+        const uint32_t len = (uint32_t)(G[u + 1] - b);
+        if (len > cap || ru >= n) {
+            if (threadIdx.x == 0) set_error(err, len > cap ? kDevTooLong : kDevBadInput);
             continue;
-        }
-        if (threadIdx.x == 0) s_fill = 0;
-        __syncthreads();
-        const uint64_t b = off[u], e = off[u + 1];
-        for (uint64_t i0 = b; i0 < e; i0 += blockDim.x) {
-            const uint64_t i = i0 + threadIdx.x;
-            uint32_t x = 0, keep = 0;
-            if (i < e && cols[i] < n) {
-                x = rank[cols[i]];
-                keep = x > ru;
-            }
-            uint32_t tot;
-            const uint32_t pos = block_excl_scan(keep, s_scan, tot);
-            if (keep && s_fill + pos < len) s_row[s_fill + pos] = x;
-            __syncthreads();
-            if (threadIdx.x == 0) s_fill += tot;
-            __syncthreads();
         }
         uint32_t p = 64;
         while (p < len) p <<= 1;
-        for (uint32_t i = len + threadIdx.x; i < p; i += blockDim.x) s_row[i] = 0xffffffffu;
+        for (uint32_t j = threadIdx.x; j < p; j += blockDim.x) s_row[j] = j < len ? vals[b + j] : 0xffffffffu;
         __syncthreads();
         bitonic_smem(s_row, p, threadIdx.x, blockDim.x, true);
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) dag_cols[ob + i] = s_row[i];
+        const uint64_t dst = dag_off[ru];
+        if (dst + len <= dag_cap)
+            for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) dag_cols[dst + j] = s_row[j];
+        else if (threadIdx.x == 0)
+            set_error(err, kDevBadInput);
         __syncthreads();
     }
 }
@@ -586,11 +603,13 @@ size_t dag_ws_bytes(uint32_t n, uint64_t arcs)
     Sizer s;
     const uint64_t ntiles = (arcs + kGoTile - 1) / kGoTile;
     s.take<uint32_t>(ntiles + 2);             // first_row
-    s.take<unsigned long long>(ntiles + 1);   // look-back status (GenOrdering)
+    s.take<unsigned long long>(ntiles + 1);   // look-back status (compaction)
     s.take<uint32_t>(8);                      // tickets, counters
-    s.take<uint32_t>((size_t)n + 1);          // rowlen (relabel)
+    s.take<uint32_t>((size_t)n + 1);          // degrees / rowlen
     s.take<unsigned long long>((size_t)n / kScTile + 2);  // look-back status (scan)
     s.take<uint32_t>((size_t)n + 1);          // long rows
+    s.take<uint64_t>((size_t)n + 1);          // kept-row offsets in input order
+    s.take<uint32_t>(arcs / 2 + 1);           // kept ranks in input order
     return s.used;
 }
 
@@ -604,23 +623,28 @@ cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, con
     uint32_t *first_row = c.take<uint32_t>(ntiles64 + 2);
     unsigned long long *status = c.take<unsigned long long>(ntiles64 + 1);
     uint32_t *ctr = c.take<uint32_t>(8);
-    uint32_t *rowlen = c.take<uint32_t>((size_t)n + 1);
+    uint32_t *keys = c.take<uint32_t>((size_t)n + 1);
     const uint32_t sc_tiles = (n + kScTile - 1) / kScTile;
     unsigned long long *sc_status = c.take<unsigned long long>((size_t)n / kScTile + 2);
     uint32_t *long_rows = c.take<uint32_t>((size_t)n + 1);
+    uint64_t *G = c.take<uint64_t>((size_t)n + 1);
+    uint32_t *kept = c.take<uint32_t>(arcs / 2 + 1);
     if (!c.ok) return cudaErrorMemoryAllocation;
     cudaError_t e;
     if ((e = cudaMemsetAsync(ctr, 0, 8 * sizeof(uint32_t), st))) return e;
     if (arcs == 0 || n == 0) {
         return cudaMemsetAsync(dag_off, 0, ((size_t)n + 1) * sizeof(uint64_t), st);
     }
+    const uint32_t ntiles = (uint32_t)ntiles64;
+    const int vec4 = ((uintptr_t)cols % 16) == 0;
+    if ((e = cudaMemsetAsync(status, 0, ntiles64 * sizeof(unsigned long long), st))) return e;
+    k_tile_rows<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, arcs, off, kGoTile, ntiles, first_row);
+    note_launches(1);
     if (!rank) {
-        const uint32_t ntiles = (uint32_t)ntiles64;
-        if ((e = cudaMemsetAsync(status, 0, ntiles64 * sizeof(unsigned long long), st))) return e;
-        k_tile_rows<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, arcs, off, kGoTile, ntiles, first_row);
-        const int vec4 = ((uintptr_t)cols % 16) == 0;
-        k_gen_ordering<<<ntiles, kGoThreads, 0, st>>>(n, arcs, off, cols, first_row, ntiles, dag_off,
-                                                     dag_cols, arcs / 2, status, ctr, err, vec4);
+        k_degrees<<<(n + 255) / 256, 256, 0, st>>>(n, off, keys);
+        k_dag_compact<0><<<ntiles, kGoThreads, 0, st>>>(n, arcs, off, cols, keys, first_row, ntiles,
+                                                       dag_off, dag_cols, arcs / 2, status, ctr,
+                                                       err, vec4);
         note_launches(2);
         if (d_max_outdeg) {
             k_max_rowlen<<<num_sms * 4, 256, 0, st>>>(n, dag_off, d_max_outdeg);
@@ -630,20 +654,25 @@ cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, con
     }
     if ((e = cudaMemsetAsync(sc_status, 0, ((size_t)sc_tiles + 1) * sizeof(unsigned long long), st)))
         return e;
+    if ((e = cudaMemsetAsync(keys, 0, ((size_t)n + 1) * sizeof(uint32_t), st))) return e;
     uint32_t *max_len = ctr + 2;
     uint32_t *n_long = ctr + 3;
-    k_outdeg_rank<<<num_sms * 8, 256, 0, st>>>(n, off, cols, rank, rowlen, max_len, err);
-    k_scan_rowlen<<<sc_tiles, kScThreads, 0, st>>>(n, rowlen, dag_off, sc_tiles, sc_status, ctr + 1,
+    k_dag_compact<1><<<ntiles, kGoThreads, 0, st>>>(n, arcs, off, cols, rank, first_row, ntiles, G,
+                                                   kept, arcs / 2, status, ctr, err, vec4);
+    k_rl_rowlen<<<(n + 255) / 256, 256, 0, st>>>(n, G, rank, keys, max_len, err);
+    k_scan_rowlen<<<sc_tiles, kScThreads, 0, st>>>(n, keys, dag_off, sc_tiles, sc_status, ctr + 1,
                                                    err);
-    k_fill_rank<<<num_sms * 8, kFrWarps * 32, 0, st>>>(n, off, cols, rank, dag_off, dag_cols,
-                                                       long_rows, n_long);
+    uint32_t rl_grid = (n + kRlRows - 1) / kRlRows;
+    if (rl_grid > (uint32_t)num_sms * 6) rl_grid = (uint32_t)num_sms * 6;
+    k_rl_sort<<<rl_grid, kRlWarps * 32, 0, st>>>(n, G, kept, rank, dag_off, dag_cols, arcs / 2,
+                                                 long_rows, n_long, err);
     const uint32_t cap_bytes = kLongCap * sizeof(uint32_t);
-    if ((e = cudaFuncSetAttribute(k_fill_rank_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_rl_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   cap_bytes)))
         return e;
-    k_fill_rank_long<<<num_sms, 1024, cap_bytes, st>>>(n, off, cols, rank, dag_off, dag_cols,
-                                                       long_rows, n_long, kLongCap, err);
-    note_launches(4);
+    k_rl_sort_long<<<num_sms, 1024, cap_bytes, st>>>(n, G, kept, rank, dag_off, dag_cols, arcs / 2,
+                                                     long_rows, n_long, kLongCap, err);
+    note_launches(5);
     if (d_max_outdeg)
         if ((e = cudaMemcpyAsync(d_max_outdeg, max_len, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)))
             return e;

@@ -1,4 +1,5 @@
-"""Parity at the full size of the R-MAT scale-20 workload (2^20 vertices, edge factor 16) in the
+"""Parity at full size: the R-MAT scale-20 workload (2^20 vertices, edge factor 16) and the
+Chung-Lu workload (4M vertices, exponent 2.1, 50 planted cliques of 20-40 vertices), in the
 launch configuration the bench times: DAG bytes against the oracle, the exact triangle count, and
 per-root counts for k = 4..6 on a seeded sample of roots the oracle can finish one by one."""
 import numpy as np
@@ -54,6 +55,52 @@ def test_sampled_roots(oracle_lib, dev, k):
     pick = np.concatenate([light[gg.permutation(k, 1, light.size)[:2000]],
                            heavy[gg.permutation(k, 2, heavy.size)[:1500]]])
     # keep roots the oracle can finish quickly (bounded work), at most 3e9 cliques in all
+    pick = pick[got[pick] <= 5e7]
+    pick = pick[np.cumsum(got[pick].astype(np.float64)) <= 3e9]
+    assert pick.size > 1000
+    _, want = oracle_lib.count_roots(off, cols, n, k, pick.astype(np.uint32), per_root=True)
+    assert np.array_equal(got[pick], want)
+
+
+# ---- Chung-Lu power law, n = 4M, avg degree 30, capped at 20,000, plus 50 planted cliques ----
+
+@pytest.fixture(scope="module")
+def chunglu():
+    return gg.config3_chung_lu()
+
+
+@pytest.fixture(scope="module")
+def dev3(gpu, chunglu):
+    return gpu.DeviceGraph(chunglu, relabel=True)
+
+
+def test_chunglu_dag_and_triangles(gpu, oracle_lib, chunglu, dev3):
+    g = chunglu
+    rank = oracle_lib.degree_rank(g.off, g.n)
+    assert np.array_equal(dev3.rank.cpu().numpy().view(np.uint32), rank)
+    off, cols = oracle_lib.dag_by_rank(g.off, g.cols, g.n, rank, relabel=True)
+    goff, gcols = dev3.dag_numpy()
+    assert np.array_equal(goff, off) and np.array_equal(gcols, cols)
+    assert dev3.count(3) == oracle_lib.count(off, cols, g.n, 3)
+
+
+@pytest.mark.parametrize("k", [5, 6])
+def test_chunglu_sampled_roots(oracle_lib, chunglu, dev3, k):
+    import math
+
+    off, cols = dev3.dag_numpy()
+    n = dev3.n
+    pr = torch.zeros(n, dtype=torch.int64, device="cuda")
+    total = dev3.count(k, per_root=pr)
+    got = pr.cpu().numpy().view(np.uint64)
+    assert int(got.sum(dtype=np.uint64)) == total
+    # every planted clique of size s contributes C(s, k) k-cliques on its own
+    assert total >= max(math.comb(s, k) for s in chunglu.meta["planted"])
+    outdeg = np.diff(off).astype(np.int64)
+    light = np.nonzero((outdeg >= k - 1) & (outdeg <= 32))[0]
+    heavy = np.nonzero(outdeg > 32)[0]
+    pick = np.concatenate([light[gg.permutation(k, 3, light.size)[:2000]],
+                           heavy[gg.permutation(k, 4, heavy.size)[:1500]]])
     pick = pick[got[pick] <= 5e7]
     pick = pick[np.cumsum(got[pick].astype(np.float64)) <= 3e9]
     assert pick.size > 1000
