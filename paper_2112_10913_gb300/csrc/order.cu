@@ -11,7 +11,7 @@
 //                         fill pass of the listing become one read of cols and one write of the DAG.
 //   Relabelled DAG from any rank (Sec. II directionalizing, rows renamed to ranks):
 //     k_dag_compact<1> (kept ranks, input row order) -> k_rl_rowlen -> k_scan_rowlen (look-back)
-//     -> k_rl_sort (per-row sort into rank order; k_rl_sort_long for rows above 1024).
+//     -> k_rl_sort (per-row sort into rank order; k_rl_sort_long for rows above 512).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -407,16 +407,74 @@ __device__ __forceinline__ uint32_t bitonic_warp(uint32_t x, int lane)
     return x;
 }
 
+// Ascending bitonic sort of 32*E values held by one warp in registers, striped: value e of
+// lane l has index e*32 + l.  Partners closer than 32 are on other lanes (shuffles), farther
+// ones are in the same lane's registers.
+template <int E>
+__device__ __forceinline__ void warp_sort_striped(uint32_t (&v)[E], int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int je = j >> 5;
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    if ((e & je) == 0) {
+                        const int e2 = e | je;
+                        const bool asc = (((uint32_t)(e * 32 + lane)) & k) == 0;
+                        const uint32_t a = v[e], b = v[e2];
+                        const bool sw = (a > b) == asc;
+                        v[e] = sw ? b : a;
+                        v[e2] = sw ? a : b;
+                    }
+                }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const bool asc = (((uint32_t)(e * 32 + lane)) & k) == 0;
+                    const uint32_t q = __shfl_xor_sync(kFull, v[e], j);
+                    v[e] = (lower == asc) ? min(v[e], q) : max(v[e], q);
+                }
+            }
+        }
+    }
+}
+
+// Loads a row of len <= 32*E values (striped, padded with the maximum), sorts it in registers
+// and stores it to dst.
+template <int E>
+__device__ __forceinline__ void warp_sort_row(const uint32_t *src, uint32_t len, uint32_t *dst, int lane)
+{
+    uint32_t v[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const uint32_t i = e * 32 + lane;
+        v[e] = i < len ? src[i] : 0xffffffffu;
+    }
+    warp_sort_striped<E>(v, lane);
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const uint32_t i = e * 32 + lane;
+        if (i < len) dst[i] = v[e];
+    }
+}
+
 constexpr int kRlWarps = 8;
-constexpr uint32_t kRlRows = 256;     // rows staged per block step
-constexpr uint32_t kRlWarpCap = 1024; // rows up to this length are sorted by one warp
+constexpr uint32_t kRlRows = 256;     // rows per block step
+constexpr uint32_t kRlStage = 8192;   // kept entries staged in shared memory per step
+constexpr uint32_t kRlWarpCap = 512;  // rows up to this length are sorted by one warp
 constexpr uint32_t kLongCap = 32768;  // longest relabelled row this build sorts (power of 2)
 
-// Relabel: kept row of input vertex u (values = ranks, input order) goes to row rank[u] of the
-// DAG, sorted.  Blocks take 256 consecutive input rows at a time; the rows' offsets, ranks and
-// destinations are staged in shared memory first (coalesced and independent loads), then each
-// warp sorts whole rows (shuffles up to 32 entries, shared memory up to 1024).  Longer rows are
-// listed for k_rl_sort_long.
+// Relabel: the kept row of input vertex u (values = ranks, input order) becomes row rank[u] of
+// the DAG, sorted.  A block takes 256 consecutive input rows at a time.  Their offsets, ranks and
+// destinations are staged in shared memory (coalesced, independent loads) and, when the rows'
+// entries fit, the entries too (one coalesced copy: the rows are contiguous).  Rows of at most
+// 32 entries are then sorted with one thread per entry: its place is the number of smaller
+// entries in its row (ranks are distinct).  Rows up to 512 entries are sorted by one warp in
+// registers (bitonic, up to 16 values per lane); longer rows are listed for k_rl_sort_long.
 __global__ __launch_bounds__(kRlWarps * 32) void k_rl_sort(
     uint32_t n, const uint64_t *__restrict__ G, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ rank, const uint64_t *__restrict__ dag_off,
@@ -425,7 +483,7 @@ __global__ __launch_bounds__(kRlWarps * 32) void k_rl_sort(
 {
     __shared__ uint64_t s_g[kRlRows + 1];
     __shared__ uint64_t s_dst[kRlRows];
-    __shared__ uint32_t s_buf[kRlWarps][kRlWarpCap];
+    __shared__ uint32_t s_vals[kRlStage];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (uint32_t r0 = blockIdx.x * kRlRows; r0 < n; r0 += gridDim.x * kRlRows) {
         const uint32_t cnt = min(kRlRows, n - r0);
@@ -436,31 +494,52 @@ __global__ __launch_bounds__(kRlWarps * 32) void k_rl_sort(
             s_dst[i] = ru < n ? dag_off[ru] : ~0ull;
         }
         __syncthreads();
+        const uint64_t base = s_g[0];
+        const uint64_t total = s_g[cnt] - base;
+        const bool staged = total <= kRlStage;
+        if (staged)
+            for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) s_vals[i] = vals[base + i];
+        __syncthreads();
+        // short rows: one thread per staged entry
+        if (staged) {
+            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+                uint32_t lo = 0, hi = cnt - 1;  // row of entry e: last i with s_g[i] - base <= e
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (s_g[mid] - base <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                const uint32_t rb = (uint32_t)(s_g[lo] - base), len = (uint32_t)(s_g[lo + 1] - s_g[lo]);
+                if (len > 32) continue;
+                const uint64_t dst = s_dst[lo];
+                if (dst == ~0ull || dst + len > dag_cap) {
+                    set_error(err, kDevBadInput);
+                    continue;
+                }
+                const uint32_t x = s_vals[e];
+                uint32_t pos = 0;
+                for (uint32_t j = 0; j < len; j++) pos += s_vals[rb + j] < x;
+                dag_cols[dst + pos] = x;
+            }
+        }
+        // longer rows (and every row of a step whose entries were not staged): one warp each
         for (uint32_t i = w; i < cnt; i += kRlWarps) {
             const uint64_t b = s_g[i];
             const uint32_t len = (uint32_t)(s_g[i + 1] - b);
+            if (len == 0 || (staged && len <= 32)) continue;
             const uint64_t dst = s_dst[i];
-            if (len == 0) continue;
-            if (dst == ~0ull || dst + len > dag_cap) {  // rank is not a permutation
+            if (dst == ~0ull || dst + len > dag_cap) {
                 if (lane == 0) set_error(err, kDevBadInput);
                 continue;
             }
-            if (len <= 32) {
-                uint32_t x = lane < len ? vals[b + lane] : 0xffffffffu;
-                x = bitonic_warp(x, lane);
-                if (lane < len) dag_cols[dst + lane] = x;
-            } else if (len <= kRlWarpCap) {
-                uint32_t *buf = s_buf[w];
-                uint32_t p = 64;
-                while (p < len) p <<= 1;
-                for (uint32_t j = lane; j < p; j += 32) buf[j] = j < len ? vals[b + j] : 0xffffffffu;
-                __syncwarp();
-                bitonic_smem(buf, p, lane, 32, false);
-                for (uint32_t j = lane; j < len; j += 32) dag_cols[dst + j] = buf[j];
-                __syncwarp();
-            } else if (lane == 0) {
-                long_rows[atomicAdd(n_long, 1u)] = r0 + i;
-            }
+            const uint32_t *src = staged ? s_vals + (b - base) : vals + b;
+            uint32_t *out = dag_cols + dst;
+            if (len <= 32) warp_sort_row<1>(src, len, out, lane);
+            else if (len <= 64) warp_sort_row<2>(src, len, out, lane);
+            else if (len <= 128) warp_sort_row<4>(src, len, out, lane);
+            else if (len <= 256) warp_sort_row<8>(src, len, out, lane);
+            else if (len <= kRlWarpCap) warp_sort_row<16>(src, len, out, lane);
+            else if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = r0 + i;
         }
     }
 }
