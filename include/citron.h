@@ -162,6 +162,33 @@ citron_status citron_count_host(uint32_t n, uint64_t arcs, const uint64_t *h_off
                                 size_t ws_bytes, void *stream);
 
 /*
+ * citron_count_batch -- exact counts of many graphs at once, each graph ("group") with its own
+ * k.  The graphs are given as ONE DAG: the DAG of their disjoint union (citron_build_dag over
+ * the union CSR; edges never cross graphs, so this is the union of the graphs' DAGs).  Each
+ * k-clique lies inside one graph and is counted once, at its first vertex (Sec. II); that
+ * root's count goes to its graph's total.  One counting pass runs per k present.
+ *   d_rank: the rank the DAG was relabelled with (NULL if the DAG keeps vertex ids).
+ *   d_group_of_vertex[v] (device, n): graph of input vertex v, < ngroups.
+ *   d_group_k[g] (device, ngroups): the k of graph g, 1..CITRON_MAX_K.
+ *   kmask (host): bit k set for every k that occurs in d_group_k (passes for other k are skipped).
+ *   max_outdeg: largest DAG row (from citron_build_dag); launch sizes derive from it.
+ *   opts: optional path thresholds (only small_max, bitmap_max, warps_per_cta, compact_max
+ *         are read); NULL for the defaults.
+ *   d_counts[g] (device, ngroups uint64, written).
+ * The call is ASYNCHRONOUS and never synchronises the host, so it can be captured into a CUDA
+ * graph and replayed; device errors stay in the workspace until citron_workspace_status.
+ */
+citron_status citron_count_batch(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
+                                 const uint32_t *d_rank, const uint32_t *d_group_of_vertex,
+                                 const uint32_t *d_group_k, uint32_t ngroups, uint32_t kmask,
+                                 uint32_t max_outdeg, const citron_count_opts *opts,
+                                 uint64_t *d_counts, void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronises `stream` and reports (then clears) the device error word of the workspace:
+ * errors recorded by asynchronous calls such as citron_count_batch or citron_build_dag. */
+citron_status citron_workspace_status(void *ws, void *stream);
+
+/*
  * citron_count_noalloc -- citron_count for callers that cannot allocate device memory.  (The
  * paper has no counterpart: this is an interface choice of this library.)
  *   Who needs it: code running while a stream is captured into a CUDA graph (allocation is not

@@ -40,6 +40,8 @@ EXPORTS = (
     "citron_host_buffer_bytes",
     "citron_count_host",
     "citron_count_noalloc",
+    "citron_count_batch",
+    "citron_workspace_status",
 )
 
 COUNT_TIME_KERNELS = 1
@@ -105,6 +107,10 @@ def lib() -> ctypes.CDLL:
     L.citron_count_host.restype = i32
     L.citron_count_noalloc.argtypes = [u32, vp, vp, u32, vp, vp]
     L.citron_count_noalloc.restype = i32
+    L.citron_count_batch.argtypes = [u32, vp, vp, vp, vp, vp, u32, u32, u32, vp, vp, vp, sz, vp]
+    L.citron_count_batch.restype = i32
+    L.citron_workspace_status.argtypes = [vp, vp]
+    L.citron_workspace_status.restype = i32
     _lib = L
     return L
 
@@ -206,6 +212,20 @@ def citron_count_noalloc(n: int, dag_off, dag_cols, k: int, stream=None) -> int:
     _check(lib().citron_count_noalloc(n, _dptr(dag_off), _dptr(dag_cols), k, ctypes.byref(out),
                                       _stream(stream)), f"citron_count_noalloc(k={k})")
     return int(out.value)
+
+
+def citron_count_batch(n: int, dag_off, dag_cols, rank, group_of_vertex, group_k, ngroups: int,
+                       kmask: int, max_outdeg: int, counts, ws, stream=None, opts: "CountOpts" = None):
+    """Asynchronous batched count (see include/citron.h); counts[g] receives graph g's count."""
+    _check(lib().citron_count_batch(n, _dptr(dag_off), _dptr(dag_cols), _dptr(rank),
+                                    _dptr(group_of_vertex), _dptr(group_k), ngroups, kmask,
+                                    max_outdeg, ctypes.byref(opts) if opts is not None else None,
+                                    _dptr(counts), _dptr(ws), _nbytes(ws), _stream(stream)),
+           "citron_count_batch")
+
+
+def citron_workspace_status(ws, stream=None):
+    _check(lib().citron_workspace_status(_dptr(ws), _stream(stream)), "citron_workspace_status")
 
 
 def citron_kernel_launches() -> int:

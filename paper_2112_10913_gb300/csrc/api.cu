@@ -29,6 +29,14 @@ void note_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relax
 unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 cudaError_t launch_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
                                     unsigned long long *per_root, cudaStream_t s);
+cudaError_t run_count_async(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
+                            uint32_t max_outdeg, CountRun &run, uint32_t *err, Carver &c,
+                            cudaStream_t s, int num_sms);
+cudaError_t launch_batch_rows(uint32_t n, const uint32_t *rank, const uint32_t *group_of_vertex,
+                              uint32_t *group_of_row, uint32_t *err, cudaStream_t s);
+cudaError_t launch_batch_trivial(uint32_t n, const uint64_t *dag_off, const uint32_t *group_of_row,
+                                 const uint32_t *group_k, uint32_t ngroups,
+                                 unsigned long long *counts, uint32_t *err, cudaStream_t s);
 }  // namespace citron_host
 
 using namespace citron_host;
@@ -119,6 +127,19 @@ const char *citron_status_str(citron_status s)
 
 int citron_version(void) { return 100; }
 
+static bool plan_from_opts(const citron_count_opts *opts, CountPlan &plan)
+{
+    if (!opts) return true;
+    if (opts->small_max > 32 || opts->bitmap_max > 1024 || opts->warps_per_cta > 32) return false;
+    if (opts->compact_max != 0 && opts->compact_max != 1 && opts->compact_max != 128) return false;
+    if (opts->small_max) plan.small_max = opts->small_max;
+    if (opts->bitmap_max) plan.bitmap_max = opts->bitmap_max;
+    if (opts->warps_per_cta) plan.warps_per_cta = opts->warps_per_cta;
+    if (opts->compact_max) plan.compact_max = opts->compact_max == 1 ? 0 : opts->compact_max;
+    if (plan.bitmap_max < plan.small_max) plan.bitmap_max = plan.small_max;
+    return true;
+}
+
 size_t citron_workspace_bytes(uint32_t n, uint64_t arcs, uint32_t max_outdeg)
 {
     if (max_outdeg == 0) {
@@ -129,7 +150,7 @@ size_t citron_workspace_bytes(uint32_t n, uint64_t arcs, uint32_t max_outdeg)
     size_t need = order_ws_bytes(n);
     size_t d = dag_ws_bytes(n, arcs);
     if (d > need) need = d;
-    size_t c = count_ws_bytes(n, max_outdeg, sm_count());
+    size_t c = count_ws_bytes(n, max_outdeg, sm_count()) + (((size_t)n + 1) * 4 + 255) / 256 * 256;
     if (c > need) need = c;
     return kHeader + need;
 }
@@ -192,17 +213,9 @@ citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint3
     (void)max_outdeg;  // the count derives every size it needs from the DAG itself
     if (!h_count || !opts || !d_dag_off || n == 0xffffffffu || k == 0) return CITRON_E_INVALID;
     if (k > CITRON_MAX_K) return CITRON_E_UNSUPPORTED;
-    if (opts->small_max > 32 || opts->bitmap_max > 1024 || opts->warps_per_cta > 32)
-        return CITRON_E_INVALID;
-    if (opts->compact_max != 0 && opts->compact_max != 1 && opts->compact_max != 128)
-        return CITRON_E_INVALID;
     CountRun run;
-    if (opts->small_max) run.plan.small_max = opts->small_max;
-    if (opts->bitmap_max) run.plan.bitmap_max = opts->bitmap_max;
-    if (opts->warps_per_cta) run.plan.warps_per_cta = opts->warps_per_cta;
-    if (opts->compact_max) run.plan.compact_max = opts->compact_max == 1 ? 0 : opts->compact_max;
-    if (run.plan.bitmap_max < run.plan.small_max) run.plan.bitmap_max = run.plan.small_max;
-    run.per_root = (unsigned long long *)opts->d_per_root;
+    if (!plan_from_opts(opts, run.plan)) return CITRON_E_INVALID;
+    run.sink.per_root = (unsigned long long *)opts->d_per_root;
     run.time_kernels = (opts->flags & CITRON_COUNT_TIME_KERNELS) != 0;
     run.count_work = (opts->flags & CITRON_COUNT_WORK) != 0;
     opts->work_ops = 0;
@@ -219,7 +232,8 @@ citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint3
             if (!e) e = cudaStreamSynchronize(s);
             *h_count = m;
         }
-        if (!e && run.per_root) e = launch_per_root_trivial(n, d_dag_off, k, run.per_root, s);
+        if (!e && run.sink.per_root)
+            e = launch_per_root_trivial(n, d_dag_off, k, run.sink.per_root, s);
         if (e) return from_cuda(e);
         return finish_sync(ws, s, CITRON_OK);
     }
@@ -247,6 +261,56 @@ citron_status citron_count(uint32_t n, const uint64_t *d_dag_off, const uint32_t
 }
 
 uint64_t citron_kernel_launches(void) { return launches(); }
+
+citron_status citron_count_batch(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
+                                 const uint32_t *d_rank, const uint32_t *d_group_of_vertex,
+                                 const uint32_t *d_group_k, uint32_t ngroups, uint32_t kmask,
+                                 uint32_t max_outdeg, const citron_count_opts *opts,
+                                 uint64_t *d_counts, void *ws, size_t ws_bytes, void *stream)
+{
+    if (n == 0xffffffffu || !d_dag_off || (n && (!d_dag_cols || !d_group_of_vertex)) ||
+        (ngroups && (!d_group_k || !d_counts)))
+        return CITRON_E_INVALID;
+    if (kmask & ~(((2u << CITRON_MAX_K) - 1) & ~1u)) return CITRON_E_UNSUPPORTED;
+    CountPlan plan;
+    if (!plan_from_opts(opts, plan)) return CITRON_E_INVALID;
+    if (!ws_ok(ws, ws_bytes, kHeader)) return CITRON_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c((char *)ws + kHeader, ws_bytes - kHeader);
+    uint32_t *group_of_row = c.take<uint32_t>((size_t)n + 1);
+    if (!c.ok) return CITRON_E_WORKSPACE;
+    unsigned long long *counts = (unsigned long long *)d_counts;
+    cudaError_t e = ngroups ? cudaMemsetAsync(counts, 0, (size_t)ngroups * 8, s) : cudaSuccess;
+    const uint32_t *gor = d_group_of_vertex;
+    if (!e && d_rank) {
+        e = launch_batch_rows(n, d_rank, d_group_of_vertex, group_of_row, err_word(ws), s);
+        gor = group_of_row;
+    }
+    if (!e && (kmask & 6u))
+        e = launch_batch_trivial(n, d_dag_off, gor, d_group_k, ngroups, counts, err_word(ws), s);
+    for (uint32_t k = 3; !e && k <= CITRON_MAX_K; k++) {
+        if (!((kmask >> k) & 1)) continue;
+        CountRun run;
+        run.plan = plan;
+        run.filter.group_of_row = gor;
+        run.filter.group_k = d_group_k;
+        run.filter.ngroups = ngroups;
+        run.filter.k = k;
+        run.sink.group_of_row = gor;
+        run.sink.group_counts = counts;
+        run.sink.ngroups = ngroups;
+        Carver cc = c;  // every pass reuses the same regions (stream-ordered)
+        e = run_count_async(n, d_dag_off, d_dag_cols, k, max_outdeg, run, err_word(ws), cc, s,
+                            sm_count());
+    }
+    return from_cuda(e);
+}
+
+citron_status citron_workspace_status(void *ws, void *stream)
+{
+    if (!ws) return CITRON_E_WORKSPACE;
+    return finish_sync(ws, (cudaStream_t)stream, CITRON_OK);
+}
 
 size_t citron_host_buffer_bytes(uint32_t n, uint64_t arcs)
 {

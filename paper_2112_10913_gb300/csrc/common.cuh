@@ -159,6 +159,42 @@ __device__ __forceinline__ unsigned long long lookback_warp(unsigned long long *
     return excl;
 }
 
+// Where a finished root's count goes, besides the grand total: the per-root array and/or the
+// total of the root's group (the graph it belongs to, in a batch of graphs).
+struct RootSink {
+    unsigned long long *per_root;        // per root (optional)
+    const uint32_t *group_of_row;        // group of each root (optional, with group_counts)
+    unsigned long long *group_counts;    // per-group totals
+    uint32_t ngroups;
+
+    __device__ __forceinline__ void put(uint32_t u, unsigned long long r, uint32_t *err) const
+    {
+        if (per_root) per_root[u] = r;
+        if (group_counts) {
+            const uint32_t g = group_of_row[u];
+            if (g < ngroups) add_checked(&group_counts[g], r, err);
+            else set_error(err, kDevBadInput);
+        }
+    }
+    __device__ __forceinline__ bool wants_root_total() const { return per_root || group_counts; }
+};
+
+// Which roots a counting pass takes, besides the out-degree prune: with group_of_row set, only
+// the roots whose group asks for this pass's k (group_k[group] == k).
+struct RootFilter {
+    const uint32_t *group_of_row = nullptr;
+    const uint32_t *group_k = nullptr;
+    uint32_t ngroups = 0;
+    uint32_t k = 0;
+
+    __device__ __forceinline__ bool takes(uint32_t u) const
+    {
+        if (!group_of_row) return true;
+        const uint32_t g = group_of_row[u];
+        return g < ngroups && group_k[g] == k;
+    }
+};
+
 }  // namespace citron
 
 // ---------------------------------------------------------------------------------------------
@@ -177,7 +213,8 @@ struct CountPlan {
 // Options and outputs of one counting call.
 struct CountRun {
     CountPlan plan;
-    unsigned long long *per_root = nullptr;  // device, optional
+    citron::RootSink sink = {nullptr, nullptr, nullptr, 0};  // per-root / per-group outputs
+    citron::RootFilter filter;                               // roots of this pass
     bool count_work = false;                 // instrumented launch: count word operations
     bool time_kernels = false;               // record device time of the counting kernels
     unsigned long long work = 0;             // out: word operations (AND + POPC of 32-bit words)

@@ -33,7 +33,7 @@ namespace citron {
 __global__ void k_classify(uint32_t n, const uint64_t *__restrict__ dag_off, uint32_t need,
                            uint32_t small_max, uint32_t bitmap_max, uint32_t *small_list,
                            uint32_t *big_list, uint32_t *mid_hist, CountStats *st,
-                           unsigned long long *per_root)
+                           unsigned long long *per_root, RootFilter filter)
 {
     __shared__ uint32_t s_cnt[2], s_base[2], s_max[3];
     const int lane = threadIdx.x & 31;
@@ -47,7 +47,7 @@ __global__ void k_classify(uint32_t n, const uint64_t *__restrict__ dag_off, uin
         const uint64_t d64 = dag_off[u + 1] - dag_off[u];
         D = (uint32_t)min(d64, (uint64_t)0xffffffffull);
         if (per_root) per_root[u] = 0;
-        if (D >= need) cls = D <= small_max ? 0 : (D <= bitmap_max ? 2 : 1);
+        if (D >= need && filter.takes(u)) cls = D <= small_max ? 0 : (D <= bitmap_max ? 2 : 1);
     }
     uint32_t off_in_warp[2] = {0, 0}, warp_base[2] = {0, 0};
 #pragma unroll
@@ -99,13 +99,13 @@ __global__ __launch_bounds__(1024) void k_mid_bins(const uint32_t *hist, uint32_
 
 __global__ void k_mid_scatter(uint32_t n, const uint64_t *__restrict__ dag_off, uint32_t need,
                               uint32_t small_max, uint32_t bitmap_max, uint32_t *cursor,
-                              uint32_t *mid_list)
+                              uint32_t *mid_list, RootFilter filter)
 {
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t D = 0xffffffffu;
     if (u < n) {
         const uint64_t d64 = dag_off[u + 1] - dag_off[u];
-        if (d64 >= need && d64 > small_max && d64 <= bitmap_max) D = (uint32_t)d64;
+        if (d64 >= need && d64 > small_max && d64 <= bitmap_max && filter.takes(u)) D = (uint32_t)d64;
     }
     const uint32_t peers = __match_any_sync(kFull, D);
     if (D == 0xffffffffu) return;
@@ -114,6 +114,36 @@ __global__ void k_mid_scatter(uint32_t n, const uint64_t *__restrict__ dag_off, 
     if ((threadIdx.x & 31) == leader) base = atomicAdd(&cursor[D], __popc(peers));
     base = __shfl_sync(peers, base, leader);
     mid_list[base + __popc(peers & lanemask_lt())] = u;
+}
+
+// Group of each DAG row: row rank[v] belongs to the group of vertex v (relabelled DAG).
+__global__ void k_batch_rows(uint32_t n, const uint32_t *__restrict__ rank,
+                             const uint32_t *__restrict__ group_of_vertex, uint32_t *group_of_row,
+                             uint32_t *err)
+{
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const uint32_t r = rank[v];
+    if (r < n) group_of_row[r] = group_of_vertex[v];
+    else set_error(err, kDevBadInput);
+}
+
+// Groups with k = 1 count their vertices, groups with k = 2 their arcs.
+__global__ void k_batch_trivial(uint32_t n, const uint64_t *__restrict__ dag_off,
+                                const uint32_t *__restrict__ group_of_row,
+                                const uint32_t *__restrict__ group_k, uint32_t ngroups,
+                                unsigned long long *group_counts, uint32_t *err)
+{
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const uint32_t g = group_of_row[u];
+    if (g >= ngroups) {
+        set_error(err, kDevBadInput);
+        return;
+    }
+    const uint32_t k = group_k[g];
+    if (k == 1) add_checked(&group_counts[g], 1ull, err);
+    else if (k == 2) add_checked(&group_counts[g], dag_off[u + 1] - dag_off[u], err);
 }
 
 __global__ void k_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
@@ -177,10 +207,11 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
     const uint32_t blocks = (n + 255) / 256;
     if (n) {
         k_classify<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max,
-                                          small_list, big_list, hist, st, run.per_root);
+                                          small_list, big_list, hist, st, run.sink.per_root,
+                                          run.filter);
         k_mid_bins<<<1, 1024, 0, s>>>(hist, plan.bitmap_max + 1, cursor, st);
         k_mid_scatter<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max,
-                                             cursor, mid_list);
+                                             cursor, mid_list, run.filter);
         note_launches(3);
     }
     CountStats hs;
@@ -212,6 +243,91 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
     *h_result = out[0];
     run.work = out[1];
     return cudaSuccess;
+}
+
+// Capture-safe variant of run_count: no host synchronisation.  Launch configurations come from
+// upper bounds (every row a root, the largest row max_outdeg) instead of the classification's
+// statistics; the kernels read the real list sizes on the device and exit when they are done.
+cudaError_t run_count_async(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
+                            uint32_t max_outdeg, CountRun &run, uint32_t *err, Carver &c,
+                            cudaStream_t s, int num_sms)
+{
+    CountStats *st = c.take<CountStats>(1);
+    unsigned long long *result = c.take<unsigned long long>(2);
+    uint32_t *next = c.take<uint32_t>(8);
+    uint32_t *small_list = c.take<uint32_t>((size_t)n + 1);
+    uint32_t *mid_list = c.take<uint32_t>((size_t)n + 1);
+    uint32_t *big_list = c.take<uint32_t>((size_t)n + 1);
+    uint32_t *hist = c.take<uint32_t>(kBitmapCap + 2);
+    uint32_t *cursor = c.take<uint32_t>(kBitmapCap + 2);
+    if (!c.ok) return cudaErrorMemoryAllocation;
+    uint32_t *list_scratch = (uint32_t *)(c.base + c.used);
+    const size_t list_words = c.cap > c.used ? (c.cap - c.used) / sizeof(uint32_t) : 0;
+    unsigned long long *work = result + 1;
+    const CountPlan &plan = run.plan;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(st, 0, sizeof(CountStats), s))) return e;
+    if ((e = cudaMemsetAsync(result, 0, 2 * sizeof(unsigned long long), s))) return e;
+    if ((e = cudaMemsetAsync(next, 0, 8 * sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(hist, 0, (kBitmapCap + 2) * sizeof(uint32_t), s))) return e;
+    if (n == 0 || max_outdeg < k - 1) return cudaSuccess;
+    const uint32_t need = k - 1;
+    const uint32_t blocks = (n + 255) / 256;
+    k_classify<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max, small_list,
+                                      big_list, hist, st, nullptr, run.filter);
+    k_mid_bins<<<1, 1024, 0, s>>>(hist, plan.bitmap_max + 1, cursor, st);
+    k_mid_scatter<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max, cursor,
+                                         mid_list, run.filter);
+    note_launches(3);
+    CountStats hs = {};
+    hs.n_small = max_outdeg >= need ? n : 0;
+    hs.max_mid = max_outdeg < plan.bitmap_max ? max_outdeg : plan.bitmap_max;
+    hs.n_mid = hs.max_mid > plan.small_max ? n : 0;
+    hs.max_big = max_outdeg;
+    hs.n_big = max_outdeg > plan.bitmap_max ? n : 0;
+    run.time_kernels = false;
+#define CITRON_CASE(KK)                                                                           \
+    case KK:                                                                                      \
+        e = launch_count_##KK(run, dag_off, dag_cols, hs, st, small_list, mid_list, big_list,     \
+                              next, list_scratch, list_words, result, work, err, s, num_sms);    \
+        break;
+    switch (k) {
+        CITRON_CASE(3)
+        CITRON_CASE(4)
+        CITRON_CASE(5)
+        CITRON_CASE(6)
+        CITRON_CASE(7)
+        CITRON_CASE(8)
+        CITRON_CASE(9)
+        CITRON_CASE(10)
+        CITRON_CASE(11)
+        CITRON_CASE(12)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CITRON_CASE
+    return e;
+}
+
+cudaError_t launch_batch_rows(uint32_t n, const uint32_t *rank, const uint32_t *group_of_vertex,
+                              uint32_t *group_of_row, uint32_t *err, cudaStream_t s)
+{
+    if (n) {
+        k_batch_rows<<<(n + 255) / 256, 256, 0, s>>>(n, rank, group_of_vertex, group_of_row, err);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_trivial(uint32_t n, const uint64_t *dag_off, const uint32_t *group_of_row,
+                                 const uint32_t *group_k, uint32_t ngroups,
+                                 unsigned long long *counts, uint32_t *err, cudaStream_t s)
+{
+    if (n) {
+        k_batch_trivial<<<(n + 255) / 256, 256, 0, s>>>(n, dag_off, group_of_row, group_k, ngroups,
+                                                       counts, err);
+        note_launches(1);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,

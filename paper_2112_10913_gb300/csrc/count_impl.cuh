@@ -63,7 +63,7 @@ template <int K>
 __global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
     const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
     const uint32_t *__restrict__ list, const CountStats *st, unsigned long long *result,
-    unsigned long long *per_root, uint32_t *err)
+    RootSink sink, uint32_t *err)
 {
     __shared__ uint32_t sL[kSmallWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -101,9 +101,9 @@ __global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
         unsigned long long acc = 0;
         const uint32_t all = D == 32 ? kFull : ((1u << D) - 1);
         small_dfs<K - 1>(all, myrow, lane, acc);
-        if (per_root) {
+        if (sink.wants_root_total()) {
             const unsigned long long r = warp_sum_u64(acc, err);
-            if (lane == 0) per_root[u] = r;
+            if (lane == 0) sink.put(u, r, err);
         }
         total += acc;
         __syncwarp();
@@ -556,7 +556,7 @@ template <int K, bool WORK>
 __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
     const uint32_t *__restrict__ list, const CountStats *st, uint32_t *next, uint32_t dcap,
-    uint32_t compact_max, unsigned long long *result, unsigned long long *per_root,
+    uint32_t compact_max, unsigned long long *result, RootSink sink,
     unsigned long long *work_out, uint32_t *err)
 {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -656,7 +656,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
                 r = s2;
             }
             if (wrapped) set_error(err, kDevOverflow);
-            if (per_root) per_root[u] = r;
+            if (sink.wants_root_total()) sink.put(u, r, err);
             const unsigned long long s2 = block_total + r;
             if (s2 < block_total) set_error(err, kDevOverflow);
             block_total = s2;
@@ -718,7 +718,7 @@ template <int K>
 __global__ __launch_bounds__(kListWarps * 32) void k_count_list(
     const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
     const uint32_t *__restrict__ list, const CountStats *st, uint32_t *next, uint32_t *scratch,
-    uint32_t stride, unsigned long long *result, unsigned long long *per_root, uint32_t *err)
+    uint32_t stride, unsigned long long *result, RootSink sink, uint32_t *err)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = blockIdx.x * kListWarps + (threadIdx.x >> 5);
@@ -739,9 +739,9 @@ __global__ __launch_bounds__(kListWarps * 32) void k_count_list(
         }
         unsigned long long acc = 0;
         list_dfs<K - 1>(dag_off, dag_cols, dag_cols + base, D, buf, stride, lane, acc);
-        if (per_root) {
+        if (sink.wants_root_total()) {
             const unsigned long long r = warp_sum_u64(acc, err);
-            if (lane == 0) per_root[u] = r;
+            if (lane == 0) sink.put(u, r, err);
         }
         total += acc;
     }
@@ -782,7 +782,7 @@ static cudaError_t launch_mid(uint32_t grid_cap, uint32_t dcap, uint32_t compact
                               size_t smem,
                               const uint64_t *dag_off, const uint32_t *dag_cols,
                               const uint32_t *mid_list, const CountStats *st, uint32_t *next,
-                              unsigned long long *result, unsigned long long *per_root,
+                              unsigned long long *result, RootSink sink,
                               unsigned long long *work, uint32_t *err, cudaStream_t s, int num_sms)
 {
     cudaError_t e;
@@ -797,7 +797,7 @@ static cudaError_t launch_mid(uint32_t grid_cap, uint32_t dcap, uint32_t compact
     uint32_t grid = (uint32_t)(num_sms * per_sm);
     if (grid > grid_cap) grid = grid_cap;
     k_count_mid<K, WORK><<<grid, warps * 32, smem, s>>>(dag_off, dag_cols, mid_list, st, next, dcap,
-                                                        compact_max, result, per_root, work, err);
+                                                        compact_max, result, sink, work, err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -831,11 +831,11 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         Timer t(run.time_kernels, s);
         if (run.count_work)
             e = launch_mid<K, true>(hs.n_mid, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
-                                    mid_list, st, next + 0, result, run.per_root, work, err, s,
+                                    mid_list, st, next + 0, result, run.sink, work, err, s,
                                     num_sms);
         else
             e = launch_mid<K, false>(hs.n_mid, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
-                                     mid_list, st, next + 0, result, run.per_root, work, err, s,
+                                     mid_list, st, next + 0, result, run.sink, work, err, s,
                                      num_sms);
         if (e) return e;
         t.stop();
@@ -847,7 +847,7 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         if (grid > cap) grid = cap;
         Timer t(run.time_kernels, s);
         k_count_small<K><<<grid, kSmallWarps * 32, 0, s>>>(dag_off, dag_cols, small_list, st, result,
-                                                           run.per_root, err);
+                                                           run.sink, err);
         note_launches(1);
         if ((e = cudaGetLastError())) return e;
         t.stop();
@@ -864,7 +864,7 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         Timer t(run.time_kernels, s);
         k_count_list<K><<<grid, kListWarps * 32, 0, s>>>(dag_off, dag_cols, big_list, st, next + 1,
                                                          list_scratch, hs.max_big, result,
-                                                         run.per_root, err);
+                                                         run.sink, err);
         note_launches(1);
         if ((e = cudaGetLastError())) return e;
         t.stop();
