@@ -350,17 +350,34 @@ class BatchItem:
 def config4_batch(seed: int = 4, count: int = 4096, n_range=(50, 50_000), deg_range=(8.0, 64.0),
                   k_range=(3, 7)) -> list[BatchItem]:
     """Many small graphs: n log-uniform, ER/R-MAT half and half, avg degree and k uniform."""
-    items = []
-    for i in range(count):
-        s = splitmix_child(seed, i)
-        ln = math.log(n_range[0]) + uniform(s, 1, 1)[0] * (math.log(n_range[1]) - math.log(n_range[0]))
-        n = int(round(math.exp(ln)))
-        deg = deg_range[0] + uniform(s, 2, 1)[0] * (deg_range[1] - deg_range[0])
-        deg = min(deg, n - 1)
-        k = int(k_range[0] + below(s, 3, 1, k_range[1] - k_range[0] + 1)[0])
-        g = small_er(s, n, deg) if below(s, 4, 1, 2)[0] == 0 else small_rmat(s, n, deg)
-        items.append(BatchItem(g, k))
-    return items
+    return [_batch_item((seed, i, n_range, deg_range, k_range)) for i in range(count)]
+
+
+def _batch_item(args):
+    seed, i, n_range, deg_range, k_range = args
+    s = splitmix_child(seed, i)
+    ln = math.log(n_range[0]) + uniform(s, 1, 1)[0] * (math.log(n_range[1]) - math.log(n_range[0]))
+    n = int(round(math.exp(ln)))
+    deg = deg_range[0] + uniform(s, 2, 1)[0] * (deg_range[1] - deg_range[0])
+    deg = min(deg, n - 1)
+    k = int(k_range[0] + below(s, 3, 1, k_range[1] - k_range[0] + 1)[0])
+    g = small_er(s, n, deg) if below(s, 4, 1, 2)[0] == 0 else small_rmat(s, n, deg)
+    return BatchItem(g, k)
+
+
+def config4_batch_parallel(seed: int = 4, count: int = 4096, n_range=(50, 50_000),
+                           deg_range=(8.0, 64.0), k_range=(3, 7), workers: int | None = None):
+    """config4_batch with the graphs generated by a pool of processes (spawned, so it is safe
+    to call at any time); the result is identical to config4_batch."""
+    import multiprocessing as mp
+    import os
+
+    workers = workers or max(1, min(32, len(os.sched_getaffinity(0))))
+    args = [(seed, i, n_range, deg_range, k_range) for i in range(count)]
+    if workers == 1:
+        return [_batch_item(a) for a in args]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_batch_item, args, chunksize=8)
 
 
 def random_small(seed: int, n: int, p: float) -> Csr:

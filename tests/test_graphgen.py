@@ -64,3 +64,10 @@ def test_batch_items():
     for it in items:
         check_csr(it.graph)
         assert 3 <= it.k <= 7 and 50 <= it.graph.n <= 400
+
+
+def test_parallel_batch_equals_serial():
+    a = gg.config4_batch(seed=9, count=6, n_range=(50, 300))
+    b = gg.config4_batch_parallel(seed=9, count=6, n_range=(50, 300), workers=2)
+    for x, y in zip(a, b):
+        assert x.k == y.k and np.array_equal(x.graph.off, y.graph.off) and np.array_equal(x.graph.cols, y.graph.cols)
