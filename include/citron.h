@@ -136,6 +136,8 @@ typedef struct {
     uint32_t compact_max;    /* in: candidate sets of the bitmap path with at most this many
                                 members are re-encoded as compact bitmaps: 0 or 128 mean 128,
                                 1 means never */
+    uint32_t max_blocks;     /* in: cap on the blocks of each counting launch, so that work on
+                                other streams keeps some SMs (0: no cap) */
     uint64_t *d_per_root;    /* in: optional device array of n uint64, as in citron_count */
     uint64_t work_ops;       /* out: 32-bit AND+POPC word operations of the bitmap path */
     float kernel_ms[3];      /* out: device ms of the warp-register, bitmap, sorted-list kernels */
@@ -172,8 +174,8 @@ citron_status citron_count_host(uint32_t n, uint64_t arcs, const uint64_t *h_off
  *   d_group_k[g] (device, ngroups): the k of graph g, 1..CITRON_MAX_K.
  *   kmask (host): bit k set for every k that occurs in d_group_k (passes for other k are skipped).
  *   max_outdeg: largest DAG row (from citron_build_dag); launch sizes derive from it.
- *   opts: optional path thresholds (only small_max, bitmap_max, warps_per_cta, compact_max
- *         are read); NULL for the defaults.
+ *   opts: optional path thresholds (only small_max, bitmap_max, warps_per_cta, compact_max,
+ *         max_blocks are read); NULL for the defaults.
  *   d_counts[g] (device, ngroups uint64, written).
  * The call is ASYNCHRONOUS and never synchronises the host, so it can be captured into a CUDA
  * graph and replayed; device errors stay in the workspace until citron_workspace_status.

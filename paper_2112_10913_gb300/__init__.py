@@ -57,6 +57,7 @@ class CountOpts(ctypes.Structure):
         ("warps_per_cta", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
         ("compact_max", ctypes.c_uint32),
+        ("max_blocks", ctypes.c_uint32),
         ("d_per_root", ctypes.c_void_p),
         ("work_ops", ctypes.c_uint64),
         ("kernel_ms", ctypes.c_float * 3),
@@ -194,11 +195,12 @@ def citron_count(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, per
 
 def citron_count_ex(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, per_root=None,
                     stream=None, small_max: int = 0, bitmap_max: int = 0, warps_per_cta: int = 0,
-                    time_kernels: bool = False, count_work: bool = False, compact_max: int = 0):
+                    time_kernels: bool = False, count_work: bool = False, compact_max: int = 0,
+                    max_blocks: int = 0):
     """Returns (count, CountOpts) -- the options carry work_ops and kernel_ms on return."""
     o = CountOpts(small_max, bitmap_max, warps_per_cta,
                   (COUNT_TIME_KERNELS if time_kernels else 0) | (COUNT_WORK if count_work else 0),
-                  compact_max, _dptr(per_root).value, 0)
+                  compact_max, max_blocks, _dptr(per_root).value, 0)
     out = ctypes.c_uint64(0)
     _check(lib().citron_count_ex(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg, ctypes.byref(o),
                                  ctypes.byref(out), _dptr(ws), _nbytes(ws), _stream(stream)),

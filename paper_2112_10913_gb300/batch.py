@@ -43,7 +43,8 @@ def union_csr(graphs: list[Csr]):
 class BatchCounter:
     """A batch of (graph, k) requests resident on one device."""
 
-    def __init__(self, graphs: list[Csr], ks: list[int], device="cuda", opts: CountOpts | None = None):
+    def __init__(self, graphs: list[Csr], ks: list[int], device="cuda", opts: CountOpts | None = None,
+                 max_blocks: int = 0):
         import torch
 
         if len(graphs) != len(ks):
@@ -55,7 +56,9 @@ class BatchCounter:
         self.kmask = 0
         for k in set(int(k) for k in ks):
             self.kmask |= 1 << k
-        self.opts = opts
+        self.max_blocks = max_blocks
+        self.opts = opts if opts is not None else (
+            CountOpts(0, 0, 0, 0, 0, max_blocks, None, 0) if max_blocks else None)
         t = torch
         self.off = t.from_numpy(u.off.view(np.int64)).to(self.dev)
         self.cols = t.from_numpy(u.cols.view(np.int32)).to(self.dev)
@@ -114,6 +117,11 @@ class BatchCounter:
 # ---------------------------------------------------------------------------------------------
 # Autotuner: picks the path thresholds for a batch by timing candidate plans on it.
 
+
+def plan_opts(plan: dict, max_blocks: int = 0) -> CountOpts:
+    return CountOpts(plan["small_max"], 0, plan["warps_per_cta"], 0, plan["compact_max"], max_blocks,
+                     None, 0)
+
 CANDIDATES = [
     dict(small_max=32, warps_per_cta=32, compact_max=0),
     dict(small_max=32, warps_per_cta=16, compact_max=0),
@@ -136,15 +144,13 @@ def tune(counter: BatchCounter, candidates=CANDIDATES, repeats: int = 2, cache: 
             known = json.loads(p.read_text())
             if key in known:
                 best = known[key]
-                counter.opts = CountOpts(best["small_max"], 0, best["warps_per_cta"], 0,
-                                         best["compact_max"], None, 0)
+                counter.opts = plan_opts(best, counter.max_blocks)
                 counter.graph = None
                 return dict(best, cached=True)
     results = []
     ref = None
     for cand in candidates:
-        counter.opts = CountOpts(cand["small_max"], 0, cand["warps_per_cta"], 0, cand["compact_max"],
-                                 None, 0)
+        counter.opts = plan_opts(cand, counter.max_blocks)
         best_ms = float("inf")
         for _ in range(repeats):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -160,7 +166,7 @@ def tune(counter: BatchCounter, candidates=CANDIDATES, repeats: int = 2, cache: 
             raise RuntimeError("tuning candidates disagree on the counts")
         results.append((best_ms, cand))
     best_ms, best = min(results, key=lambda r: r[0])
-    counter.opts = CountOpts(best["small_max"], 0, best["warps_per_cta"], 0, best["compact_max"], None, 0)
+    counter.opts = plan_opts(best, counter.max_blocks)
     counter.graph = None
     out = dict(best, ms=best_ms, tried=[dict(c, ms=m) for m, c in results])
     if cache and key:

@@ -136,6 +136,7 @@ static bool plan_from_opts(const citron_count_opts *opts, CountPlan &plan)
     if (opts->bitmap_max) plan.bitmap_max = opts->bitmap_max;
     if (opts->warps_per_cta) plan.warps_per_cta = opts->warps_per_cta;
     if (opts->compact_max) plan.compact_max = opts->compact_max == 1 ? 0 : opts->compact_max;
+    plan.max_blocks = opts->max_blocks;
     if (plan.bitmap_max < plan.small_max) plan.bitmap_max = plan.small_max;
     return true;
 }

@@ -208,6 +208,7 @@ struct CountPlan {
     uint32_t bitmap_max = 1024;    // ... <= this use the shared-memory bitmap path
     uint32_t warps_per_cta = 32;   // warps per block of the bitmap path (fewer if shared memory is short)
     uint32_t compact_max = 128;    // candidate sets up to this size are re-encoded compactly (0: never)
+    uint32_t max_blocks = 0;       // cap on the blocks of each counting launch (0: no cap)
 };
 
 // Options and outputs of one counting call.

@@ -778,8 +778,8 @@ struct Timer {
 };
 
 template <int K, bool WORK>
-static cudaError_t launch_mid(uint32_t grid_cap, uint32_t dcap, uint32_t compact_max, uint32_t warps,
-                              size_t smem,
+static cudaError_t launch_mid(uint32_t grid_cap, uint32_t block_cap, uint32_t dcap,
+                              uint32_t compact_max, uint32_t warps, size_t smem,
                               const uint64_t *dag_off, const uint32_t *dag_cols,
                               const uint32_t *mid_list, const CountStats *st, uint32_t *next,
                               unsigned long long *result, RootSink sink,
@@ -796,6 +796,7 @@ static cudaError_t launch_mid(uint32_t grid_cap, uint32_t dcap, uint32_t compact
     if (per_sm < 1) per_sm = 1;
     uint32_t grid = (uint32_t)(num_sms * per_sm);
     if (grid > grid_cap) grid = grid_cap;
+    if (block_cap && grid > block_cap) grid = block_cap;
     k_count_mid<K, WORK><<<grid, warps * 32, smem, s>>>(dag_off, dag_cols, mid_list, st, next, dcap,
                                                         compact_max, result, sink, work, err);
     note_launches(1);
@@ -830,11 +831,11 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         while (warps > 1 && smem_for(warps) > (size_t)smem_cap) warps--;
         Timer t(run.time_kernels, s);
         if (run.count_work)
-            e = launch_mid<K, true>(hs.n_mid, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
+            e = launch_mid<K, true>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
                                     mid_list, st, next + 0, result, run.sink, work, err, s,
                                     num_sms);
         else
-            e = launch_mid<K, false>(hs.n_mid, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
+            e = launch_mid<K, false>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
                                      mid_list, st, next + 0, result, run.sink, work, err, s,
                                      num_sms);
         if (e) return e;
@@ -843,7 +844,8 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
     }
     if (hs.n_small) {
         uint32_t grid = (hs.n_small + kSmallWarps - 1) / kSmallWarps;
-        const uint32_t cap = (uint32_t)num_sms * 16;
+        uint32_t cap = (uint32_t)num_sms * 16;
+        if (plan.max_blocks && cap > plan.max_blocks * 4) cap = plan.max_blocks * 4;
         if (grid > cap) grid = cap;
         Timer t(run.time_kernels, s);
         k_count_small<K><<<grid, kSmallWarps * 32, 0, s>>>(dag_off, dag_cols, small_list, st, result,
@@ -858,7 +860,8 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         size_t warps = per_warp ? list_scratch_words / per_warp : 0;
         if (warps < kListWarps) return cudaErrorMemoryAllocation;
         uint32_t grid = (uint32_t)(warps / kListWarps);
-        const uint32_t cap = (uint32_t)num_sms;
+        uint32_t cap = (uint32_t)num_sms;
+        if (plan.max_blocks && cap > plan.max_blocks) cap = plan.max_blocks;
         if (grid > cap) grid = cap;
         if (grid > (hs.n_big + kListWarps - 1) / kListWarps) grid = (hs.n_big + kListWarps - 1) / kListWarps;
         Timer t(run.time_kernels, s);

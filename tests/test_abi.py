@@ -55,10 +55,10 @@ def test_argument_checks_need_no_gpu(built):
     assert L.citron_count(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 13, 0, ctypes.byref(out), null, null, 0, null) == 6
     assert L.citron_count(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 3, 0, null, null, null, 0, null) == 1
     # citron_count_ex: options are required; thresholds are range-checked
-    o = cg.CountOpts(40, 0, 0, 0, 0, None, 0)
+    o = cg.CountOpts(40, 0, 0, 0, 0, 0, None, 0)
     assert L.citron_count_ex(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 3, 0, null, ctypes.byref(out), null, 0, null) == 1
     assert L.citron_count_ex(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 3, 0, ctypes.byref(o), ctypes.byref(out), null, 0, null) == 1
-    o = cg.CountOpts(0, 0, 0, 0, 100, None, 0)  # compact_max must be 0, 1, 128 or 256
+    o = cg.CountOpts(0, 0, 0, 0, 100, 0, None, 0)  # compact_max must be 0, 1, 128 or 256
     assert L.citron_count_ex(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 3, 0, ctypes.byref(o), ctypes.byref(out), null, 0, null) == 1
     assert L.citron_kernel_launches() == 0
     # no workspace
