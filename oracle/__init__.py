@@ -64,6 +64,8 @@ def lib():
         L.oracle_dag_by_rank.restype = None
         L.oracle_core_rank.argtypes = [u32, p, p, p]
         L.oracle_core_rank.restype = None
+        L.oracle_core_rank_rounds.argtypes = [u32, p, p, p, p, p]
+        L.oracle_core_rank_rounds.restype = None
         L.oracle_count.argtypes = [u32, p, p, i32, i32, p]
         L.oracle_count.restype = i32
         L.oracle_count_roots.argtypes = [u32, p, p, i32, p, u64, i32, p, p]
@@ -108,6 +110,16 @@ def core_rank(off, cols, n: int) -> np.ndarray:
     rank = np.zeros(n, dtype=np.uint32)
     lib().oracle_core_rank(n, _ptr(off), _ptr(cols), _ptr(rank))
     return rank
+
+
+def core_rank_rounds(off, cols, n: int):
+    """Core ordering by synchronous peeling rounds: (rank, degeneracy, rounds)."""
+    off, cols = _c(off, np.uint64), _c(cols, np.uint32)
+    rank = np.zeros(n, dtype=np.uint32)
+    level, rounds = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    lib().oracle_core_rank_rounds(n, _ptr(off), _ptr(cols), _ptr(rank), ctypes.byref(level),
+                                  ctypes.byref(rounds))
+    return rank, int(level.value), int(rounds.value)
 
 
 def gen_ordering(off, cols, n: int):

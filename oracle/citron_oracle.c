@@ -183,6 +183,50 @@ void oracle_core_rank(uint32_t n, const uint64_t *off, const uint32_t *cols, uin
     free(gone);
 }
 
+/* Core ordering by synchronous peeling rounds: the parallel form of Algorithm OrdCore that the
+ * GPU computes.  level starts at 0; every round first raises level to the smallest remaining
+ * degree (it never falls), then removes ALL remaining vertices whose remaining degree is at most
+ * level, together, and only then lowers their remaining neighbours' degrees.  rank[u] orders the
+ * vertices by (removal round, id).  A vertex's out-neighbours (rank[u] < rank[v]) were all
+ * present when its round began, so its out-degree is at most the level of that round, which never
+ * exceeds the degeneracy: the maximum out-degree is the degeneracy, as with the sequential order.
+ * The final level (the degeneracy) and the number of rounds are returned.  Plain O(rounds * n + m). */
+void oracle_core_rank_rounds(uint32_t n, const uint64_t *off, const uint32_t *cols, uint32_t *rank,
+                             uint32_t *out_level, uint32_t *out_rounds)
+{
+    uint64_t *cur = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+    char *gone = (char *)calloc(n ? n : 1, 1);
+    char *now = (char *)calloc(n ? n : 1, 1);
+    uint64_t level = 0;
+    uint32_t removed = 0, rounds = 0;
+    for (uint32_t u = 0; u < n; u++) cur[u] = degree(off, u);
+    while (removed < n) {
+        uint64_t least = UINT64_MAX;
+        for (uint32_t u = 0; u < n; u++)
+            if (!gone[u] && cur[u] < least) least = cur[u];
+        if (least > level) level = least;
+        for (uint32_t u = 0; u < n; u++) /* this round's vertices, in id order */
+            if (!gone[u] && cur[u] <= level) {
+                now[u] = 1;
+                rank[u] = removed++;
+            }
+        for (uint32_t u = 0; u < n; u++)
+            if (now[u]) gone[u] = 1;
+        for (uint32_t u = 0; u < n; u++)
+            if (now[u]) {
+                for (uint64_t e = off[u]; e < off[u + 1]; e++)
+                    if (!gone[cols[e]]) cur[cols[e]] -= 1;
+                now[u] = 0;
+            }
+        rounds++;
+    }
+    if (out_level) *out_level = (uint32_t)level;
+    if (out_rounds) *out_rounds = rounds;
+    free(cur);
+    free(gone);
+    free(now);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Counting phase (Sec. III Algorithm "Counting"; Sec. V-B subgraph build and heuristics).    */
 

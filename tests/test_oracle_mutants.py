@@ -25,6 +25,8 @@ MUTANTS = [
     ("recursion-depth", "int st = cnt(g, next, len2, r - 1, levels + 1, &part);", "int st = cnt(g, next, len2, r - 2 > 0 ? r - 2 : 1, levels + 1, &part);"),
     ("root-level", "st = cnt(p->g, nu, du, p->k - 1, levels, &c);", "st = cnt(p->g, nu, du, p->k, levels, &c);"),
     ("fill-transposed", "if (degree_before(off, u, cols[e])) dag_cols[pos++] = cols[e];", "if (degree_before(off, cols[e], u)) dag_cols[pos++] = cols[e];"),
+    ("rounds-level-falls", "if (least > level) level = least;", "level = least;"),
+    ("rounds-stale-members", "                now[u] = 0;\n", ""),
     ("prefix-sum", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u];", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u] - (count[u] > 2);"),
 ]
 
@@ -57,9 +59,31 @@ def pins_hold() -> bool:
         g = gg.complete_multipartite(parts)
         if oracle.count_graph(g, 3, threads=1) != 4 * 3 * 3 + 4 * 3 * 2 + 4 * 3 * 2 + 3 * 3 * 2:
             return False
+        # core ordering by rounds: a hand-worked example and the degeneracy on random graphs
+        g = gg.csr_from_edges(6, np.array([0, 0, 0, 1, 1, 2, 3, 4], dtype=np.uint32),
+                              np.array([1, 2, 3, 2, 3, 3, 4, 5], dtype=np.uint32))
+        rank, level, rounds = oracle.core_rank_rounds(g.off, g.cols, g.n)
+        if rank.tolist() != [2, 3, 4, 5, 1, 0] or level != 3 or rounds != 3:
+            return False
+        for seed in (1, 2, 3, 4, 5):
+            g = gg.random_small(seed, 12, 0.4)
+            rank, level, _ = oracle.core_rank_rounds(g.off, g.cols, g.n)
+            off, _ = oracle.dag_by_rank(g.off, g.cols, g.n, rank, relabel=False)
+            if not int(np.diff(off).max()) == level == degeneracy(g):
+                return False
         return True
     except Exception:
         return False
+
+
+def degeneracy(g) -> int:
+    """Largest minimum degree over all induced subgraphs (brute force, n <= 12)."""
+    adj = [set(g.cols[g.off[v]: g.off[v + 1]].tolist()) for v in range(g.n)]
+    best = 0
+    for mask in range(1, 1 << g.n):
+        s = {v for v in range(g.n) if mask >> v & 1}
+        best = max(best, min(len(adj[v] & s) for v in s))
+    return best
 
 
 def test_unmutated_oracle_passes_battery():

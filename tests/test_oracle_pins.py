@@ -186,6 +186,7 @@ def orderings(oracle_lib, g):
     yield "identity", np.arange(g.n, dtype=np.uint32)
     yield "random", np.argsort(gg.draws_u64(77, 1, g.n)).astype(np.uint32).argsort().astype(np.uint32)
     yield "core", oracle_lib.core_rank(g.off, g.cols, g.n)
+    yield "core_rounds", oracle_lib.core_rank_rounds(g.off, g.cols, g.n)[0]
 
 
 @pytest.mark.parametrize("make", [lambda: gg.config1_er_planted(), lambda: gg.small_rmat(9, 1500, 30.0),
@@ -270,6 +271,46 @@ def test_core_order_minimises_max_outdegree(oracle_lib, seed):
     mc, md = int(np.diff(off_c).max()), int(np.diff(off_d).max())
     assert mc == degeneracy_brute(g)
     assert mc <= md
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_core_rounds_order_reaches_the_degeneracy(oracle_lib, seed):
+    g = gg.random_small(seed, 13, 0.4)
+    rank, level, rounds = oracle_lib.core_rank_rounds(g.off, g.cols, g.n)
+    assert sorted(rank.tolist()) == list(range(g.n))
+    off, _ = oracle_lib.dag_by_rank(g.off, g.cols, g.n, rank, relabel=False)
+    assert int(np.diff(off).max()) == level == degeneracy_brute(g)
+    assert 1 <= rounds <= g.n
+
+
+def _graph(n, edges):
+    u = np.array([a for a, _ in edges], dtype=np.uint32)
+    v = np.array([b for _, b in edges], dtype=np.uint32)
+    return gg.csr_from_edges(n, u, v)
+
+
+# rounds worked out by hand from the definition (remove every vertex of remaining degree <= level
+# together, level = max(level, smallest remaining degree), ties by id)
+@pytest.mark.parametrize("name,n,edges,want_rank,want_level,want_rounds", [
+    ("path7", 7, [(i, i + 1) for i in range(6)], [0, 2, 4, 6, 5, 3, 1], 1, 4),
+    ("star5", 6, [(0, i) for i in range(1, 6)], [5, 0, 1, 2, 3, 4], 1, 2),
+    ("cycle6", 6, [(i, (i + 1) % 6) for i in range(6)], [0, 1, 2, 3, 4, 5], 2, 1),
+    ("k5", 5, [(i, j) for i in range(5) for j in range(i + 1, 5)], [0, 1, 2, 3, 4], 4, 1),
+    ("lollipop", 6, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3), (3, 4), (4, 5)],
+     [2, 3, 4, 5, 1, 0], 3, 3),
+])
+def test_core_rounds_hand_examples(oracle_lib, name, n, edges, want_rank, want_level, want_rounds):
+    g = _graph(n, edges)
+    rank, level, rounds = oracle_lib.core_rank_rounds(g.off, g.cols, g.n)
+    assert rank.tolist() == want_rank and level == want_level and rounds == want_rounds, name
+
+
+def test_fig1_core_value_by_rounds(oracle_lib):
+    gold = read_golden("fig1.txt")
+    g = gg.fig1()
+    rank, level, _ = oracle_lib.core_rank_rounds(g.off, g.cols, g.n)
+    off, _ = oracle_lib.dag_by_rank(g.off, g.cols, g.n, rank, relabel=False)
+    assert int(np.diff(off).max()) == level == gold["core_value"][0][0]
 
 
 def test_gen_ordering_keeps_each_edge_once(oracle_lib):
