@@ -64,6 +64,8 @@ def lib():
         L.oracle_dag_by_rank.restype = None
         L.oracle_core_rank.argtypes = [u32, p, p, p]
         L.oracle_core_rank.restype = None
+        L.oracle_list.argtypes = [u32, p, p, i32, p, u64, p]
+        L.oracle_list.restype = i32
         L.oracle_core_rank_rounds.argtypes = [u32, p, p, p, p, p]
         L.oracle_core_rank_rounds.restype = None
         L.oracle_count.argtypes = [u32, p, p, i32, i32, p]
@@ -156,6 +158,19 @@ def count_roots(dag_off, dag_cols, n: int, k: int, roots, threads: int | None = 
     _check(lib().oracle_count_roots(n, _ptr(dag_off), _ptr(dag_cols), k, _ptr(roots), roots.size,
                                     threads or default_threads(), _ptr(pr), _ptr(out)))
     return (int(out[0]), pr[: roots.size]) if per_root else int(out[0])
+
+
+def list_cliques(dag_off, dag_cols, n: int, k: int, capacity: int | None = None) -> np.ndarray:
+    """Every k-clique as a row of k DAG ids in recursion order (root first); shape (K_k, k)."""
+    dag_off, dag_cols = _c(dag_off, np.uint64), _c(dag_cols, np.uint32)
+    total = ctypes.c_uint64(0)
+    if capacity is None:
+        _check(lib().oracle_list(n, _ptr(dag_off), _ptr(dag_cols), k, None, 0, ctypes.byref(total)))
+        capacity = int(total.value)
+    out = np.zeros((max(1, capacity), k), dtype=np.uint32)
+    _check(lib().oracle_list(n, _ptr(dag_off), _ptr(dag_cols), k, _ptr(out), capacity,
+                             ctypes.byref(total)))
+    return out[: min(capacity, int(total.value))]
 
 
 def count_per_edge(dag_off, dag_cols, n: int, k: int) -> np.ndarray:

@@ -397,6 +397,72 @@ int oracle_count_roots(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_
     return count_roots(n, dag_off, dag_adj, k, roots, nroots, threads, per_root, out);
 }
 
+/* Listing instead of counting (Sec. VIII: the counting recursion enumerates each clique once).
+ * Every k-clique is written as k DAG ids in recursion order: its first vertex u, then the
+ * vertices chosen level by level (for a DAG whose rows are sorted, ascending order along the
+ * DAG's order).  The recursion is cnt()'s with the r = 2 shortcut replaced by a walk over the
+ * last level's members.  Writes at most `capacity` cliques; *total receives how many exist. */
+typedef struct {
+    const dag_t *g;
+    int k;
+    uint32_t *out;
+    uint64_t capacity, total;
+    uint32_t *prefix;
+} lister_t;
+
+static void list_rec(lister_t *L, const uint32_t *C, uint32_t len, int r, uint32_t **levels)
+{
+    if (len < (uint32_t)r) return;
+    int depth = L->k - r; /* vertices already chosen */
+    for (uint32_t i = 0; i < len; i++) {
+        uint32_t a = C[i];
+        L->prefix[depth] = a;
+        if (r == 1) {
+            if (L->total < L->capacity)
+                memcpy(L->out + L->total * (uint64_t)L->k, L->prefix, sizeof(uint32_t) * (size_t)L->k);
+            L->total++;
+            continue;
+        }
+        const uint32_t *na = L->g->adj + L->g->off[a];
+        uint64_t da = L->g->off[a + 1] - L->g->off[a];
+        uint32_t *next = levels[0];
+        uint32_t len2 = intersect(C, len, na, da, next);
+        list_rec(L, next, len2, r - 1, levels + 1);
+    }
+}
+
+int oracle_list(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_adj, int k, uint32_t *out,
+                uint64_t capacity, uint64_t *total)
+{
+    *total = 0;
+    if (k < 1 || k > 64) return ORACLE_E_ARG;
+    dag_t g = {n, dag_off, dag_adj};
+    uint32_t width = max_row(&g);
+    uint32_t *store = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)width + 1) * (size_t)k);
+    uint32_t **levels = (uint32_t **)malloc(sizeof(uint32_t *) * (size_t)k);
+    uint32_t prefix[64];
+    if (!store || !levels) {
+        free(store);
+        free(levels);
+        return ORACLE_E_NOMEM;
+    }
+    for (int i = 0; i < k; i++) levels[i] = store + (size_t)i * (width + 1);
+    lister_t L = {&g, k, out, capacity, 0, prefix};
+    for (uint32_t u = 0; u < n; u++) {
+        prefix[0] = u; /* the root; its candidates are N+(u) */
+        if (k == 1) {
+            if (L.total < capacity) out[L.total] = u;
+            L.total++;
+            continue;
+        }
+        list_rec(&L, dag_adj + dag_off[u], (uint32_t)(dag_off[u + 1] - dag_off[u]), k - 1, levels);
+    }
+    *total = L.total;
+    free(store);
+    free(levels);
+    return ORACLE_OK;
+}
+
 /* Edge-level form used to localise differences: for DAG arc e = (u, v), the number of k-cliques
  * whose first two vertices in the DAG order are u then v, i.e. cnt(N+(u) ∩ N+(v), k-2) (k >= 3). */
 int oracle_count_per_edge(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_adj, int k,

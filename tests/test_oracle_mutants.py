@@ -2,6 +2,7 @@
 comparison, a dropped element, an off-by-one, a transposed operand), compile each mutant on the
 CPU and check that at least one pin fails for it.  The oracle source itself is never changed."""
 import ctypes
+import itertools
 import math
 import subprocess
 from pathlib import Path
@@ -27,6 +28,7 @@ MUTANTS = [
     ("fill-transposed", "if (degree_before(off, u, cols[e])) dag_cols[pos++] = cols[e];", "if (degree_before(off, cols[e], u)) dag_cols[pos++] = cols[e];"),
     ("rounds-level-falls", "if (least > level) level = least;", "level = least;"),
     ("rounds-stale-members", "                now[u] = 0;\n", ""),
+    ("list-depth", "int depth = L->k - r; /* vertices already chosen */", "int depth = L->k - r - (r > 2);"),
     ("prefix-sum", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u];", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u] - (count[u] > 2);"),
 ]
 
@@ -70,6 +72,18 @@ def pins_hold() -> bool:
             rank, level, _ = oracle.core_rank_rounds(g.off, g.cols, g.n)
             off, _ = oracle.dag_by_rank(g.off, g.cols, g.n, rank, relabel=False)
             if not int(np.diff(off).max()) == level == degeneracy(g):
+                return False
+        # listing: every row a distinct clique, as many as the brute-force count
+        g = gg.random_small(2, 12, 0.6)
+        off, cols = oracle.gen_ordering(g.off, g.cols, g.n)
+        adj = [set(g.cols[g.off[v]: g.off[v + 1]].tolist()) for v in range(g.n)]
+        for k in (3, 4, 5):
+            rows = [tuple(r.tolist()) for r in oracle.list_cliques(off, cols, g.n, k)]
+            want = sum(1 for s in itertools.combinations(range(g.n), k)
+                       if all(b in adj[a] for a, b in itertools.combinations(s, 2)))
+            if len(rows) != want or len({frozenset(r) for r in rows}) != want:
+                return False
+            if any(b not in adj[a] for r in rows for a, b in itertools.combinations(r, 2)):
                 return False
         return True
     except Exception:

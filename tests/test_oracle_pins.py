@@ -342,3 +342,41 @@ def test_validate_catches_defects(oracle_lib):
     bad = g.cols.copy()
     bad[2] = 9
     assert oracle_lib.validate(g.off, bad, g.n) == 2
+
+
+# -- listing (Sec. VIII: the counting recursion enumerates every clique once) ------------------
+
+
+def brute_cliques(g, k):
+    adj = adjacency_sets(g)
+    return {frozenset(s) for s in itertools.combinations(range(g.n), k)
+            if all(b in adj[a] for a, b in itertools.combinations(s, 2))}
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("relabel", [False, True])
+def test_listing_is_the_set_of_all_cliques(oracle_lib, seed, relabel):
+    g = gg.random_small(seed, 14, 0.6)
+    rank = oracle_lib.degree_rank(g.off, g.n)
+    off, cols = oracle_lib.dag_by_rank(g.off, g.cols, g.n, rank, relabel)
+    inv = np.argsort(rank) if relabel else np.arange(g.n)
+    for k in range(1, 8):
+        rows = oracle_lib.list_cliques(off, cols, g.n, k)
+        got = [frozenset(inv[r].tolist()) for r in rows]
+        assert len(got) == len(set(got)) == brute_count(g, k)
+        assert set(got) == brute_cliques(g, k)
+        # each row follows DAG arcs: every later vertex is an out-neighbour of every earlier one
+        for r in rows[:200]:
+            for i in range(k):
+                for j in range(i + 1, k):
+                    assert r[j] in cols[off[r[i]]: off[r[i] + 1]]
+
+
+def test_listing_fig1_and_capacity(oracle_lib):
+    g = gg.fig1()
+    off, cols = oracle_lib.gen_ordering(g.off, g.cols, g.n)
+    tri = oracle_lib.list_cliques(off, cols, g.n, 3)
+    assert {frozenset(r.tolist()) for r in tri} == brute_cliques(g, 3) and len(tri) == 5
+    assert [set(r.tolist()) for r in oracle_lib.list_cliques(off, cols, g.n, 4)] == [{0, 1, 3, 4}]
+    part = oracle_lib.list_cliques(off, cols, g.n, 3, capacity=2)
+    assert part.tolist() == tri[:2].tolist()
