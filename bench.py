@@ -47,8 +47,11 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-budget", type=float, default=6.0, help="seconds of oracle counting per k")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="rmat20", choices=["rmat20", "batch", "serve"],
-                   help="rmat20: order+count edges/s (default); batch: 4,096-graph batched graphs/s")
+    p.add_argument("--workload", default="rmat20",
+                   choices=["rmat20", "batch", "serve", "orderings", "list", "chunglu"],
+                   help="rmat20: order+count edges/s (default); batch: 4,096-graph batched graphs/s; "
+                        "serve: request loop; orderings: degree vs core ordering; list: clique "
+                        "listing; chunglu: the 4M-vertex power-law graph, k=5..9")
     p.add_argument("--batch-graphs", type=int, default=4096)
     return p.parse_args()
 
@@ -460,7 +463,11 @@ def run_serve(args):
     big = [gg.config2_rmat(seed=50 + i, scale=18, edge_factor=16) for i in range(2)]
     for j in range(0, per_rate, 50):  # 2 % of the requests
         pool[j] = gg.BatchItem(big[(j // 50) % 2], pool[j].k)
-    alone = [cg.DeviceGraph(it.graph).count(it.k) for it in pool]
+    alone, alone_ms = [], []
+    for it in pool:  # each request served alone (upload, order, DAG, count): the latency floor
+        t0 = time.perf_counter()
+        alone.append(cg.DeviceGraph(it.graph).count(it.k))
+        alone_ms.append((time.perf_counter() - t0) * 1e3)
     results = {}
     cfg = ServeConfig(slots=4, max_batch_requests=64)
     for rate in (25, 100, 500, 1000, 2000, 5000):
@@ -484,6 +491,175 @@ def run_serve(args):
                    "slots": cfg.slots, "max_batch_requests": cfg.max_batch_requests,
                    "heavy_arcs": cfg.heavy_arcs, "heavy_sm_fraction": cfg.heavy_sm_fraction},
         "per_rate": results, "counts_equal_alone": True,
+        "alone_latency_ms": {"p50": float(np.percentile(alone_ms, 50)),
+                             "p99": float(np.percentile(alone_ms, 99)),
+                             "sum_s": float(sum(alone_ms) / 1e3)},
+    }
+
+
+def _events_ms(fn, reps: int = 3) -> float:
+    """Mean device time (ms) of fn() over reps runs, CUDA events on the current stream."""
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_orderings(args):
+    """Degree ordering (CITRON, Sec. IV) against the core ordering (Sec. III, computed in
+    synchronous rounds) on R-MAT scale 20: ordering time, DAG time, maximum out-degree and the
+    counting time it leads to (the comparison of Table II and Table III)."""
+    import torch
+
+    from paper_2112_10913_gb300 import build as B
+
+    B.build()
+    import paper_2112_10913_gb300 as cg
+
+    g = workload()
+    dev = torch.device("cuda")
+    off = torch.from_numpy(g.off.view(np.int64)).to(dev)
+    cols = torch.from_numpy(g.cols.view(np.int32)).to(dev)
+    ws = cg.alloc_workspace(g.n, g.arcs, 1024, device=dev)
+    rank = torch.empty(g.n, dtype=torch.int32, device=dev)
+    dag_off = torch.empty(g.n + 1, dtype=torch.int64, device=dev)
+    dag_cols = torch.empty(g.arcs // 2, dtype=torch.int32, device=dev)
+    ks = [int(x) for x in args.ks.split(",") if x]
+    out = {}
+    for name in ("degree", "core"):
+        info = {}
+        if name == "degree":
+            order = lambda: cg.citron_order(g.n, off, rank, None, ws)
+        else:
+            def order():
+                info["degeneracy"], info["rounds"] = cg.citron_core_order(g.n, off, cols, rank, None, ws)
+        t_order = _events_ms(order)
+        t_dag = _events_ms(lambda: cg.citron_build_dag(g.n, off, cols, rank, dag_off, dag_cols, ws,
+                                                      want_max_outdeg=False))
+        mx = cg.citron_build_dag(g.n, off, cols, rank, dag_off, dag_cols, ws)
+        counts = {}
+        for k in ks:
+            c, o = cg.citron_count_ex(g.n, dag_off, dag_cols, k, ws, mx, None, None, time_kernels=True)
+            t = _events_ms(lambda: cg.citron_count(g.n, dag_off, dag_cols, k, ws, mx), reps=1)
+            counts[str(k)] = dict(count=c, count_ms=t)
+        out[name] = dict(order_ms=t_order, dag_ms=t_dag, max_outdeg=mx, per_k=counts, **info)
+    for k in ks:
+        assert out["degree"]["per_k"][str(k)]["count"] == out["core"]["per_k"][str(k)]["count"]
+    d, c = out["degree"], out["core"]
+    return {
+        "metric": "ordering comparison (Table II/III analogue): order ms, max out-degree, count ms",
+        "value": c["order_ms"] / d["order_ms"], "unit": "core/degree ordering time ratio",
+        "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": None, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 (exact integer)",
+        "data": "synthetic (seeded R-MAT)",
+        "config": {"workload": "rmat20-ef16", "n": g.n, "m_undirected": g.m, "ks": ks},
+        "orderings": out,
+    }
+
+
+def run_list(args):
+    """Listing (Sec. VIII): every k-clique written out as k ids, on R-MAT scale 20 for k = 3 and
+    4 (the output must fit in HBM).  Bound: the output writes (k x 4 bytes per clique)."""
+    import torch
+
+    from paper_2112_10913_gb300 import build as B
+
+    B.build()
+    import paper_2112_10913_gb300 as cg
+
+    g = workload()
+    dg = cg.DeviceGraph(g)
+    peak = _hbm_peak()
+    res = {}
+    for k in (3, 4):
+        total = cg.citron_list(dg.n, dg.dag_off, dg.dag_cols, k, dg.ws)
+        if total * k * 4 > (64 << 30):
+            res[str(k)] = dict(cliques=total, skipped="output above 64 GiB")
+            continue
+        out_t = torch.empty((total, k), dtype=torch.int32, device="cuda")
+        ms = _events_ms(lambda: cg.citron_list(dg.n, dg.dag_off, dg.dag_cols, k, dg.ws, out_t), reps=3)
+        assert total == dg.count(k)
+        gbs = total * k * 4 / (ms * 1e-3) / 1e9
+        res[str(k)] = dict(cliques=total, ms=ms, cliques_per_s=total / (ms * 1e-3), out_gb_s=gbs,
+                           frac_of_hbm=gbs / peak)
+        del out_t
+        torch.cuda.empty_cache()
+    top = res.get("4", res["3"])
+    return {
+        "metric": "k-clique listing (cliques/s; output GB/s)", "value": top.get("cliques_per_s"),
+        "unit": "cliques/s", "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": top.get("ms"),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 ids", "data": "synthetic (seeded R-MAT)",
+        "config": {"workload": "rmat20-ef16 listing k=3,4 (DAG ids mapped to none)", "n": g.n},
+        "roofline": {"bound": "hbm", "achieved": top.get("out_gb_s"), "peak": peak, "unit": "GB/s",
+                     "frac": top.get("frac_of_hbm"), "traffic": None,
+                     "note": "algorithmic bytes = the rows written (k x 4 B per clique)"},
+        "per_k": res,
+    }
+
+
+def run_chunglu(args):
+    """The 4M-vertex Chung-Lu workload (exponent 2.1, avg degree 30, degrees capped at 20,000,
+    50 planted cliques of 20-40 vertices): order + relabelled DAG + count per k, k = 5..9 while a
+    count stays under a minute; per-root share of the heaviest roots (load balance)."""
+    import torch
+
+    from paper_2112_10913_gb300 import build as B
+
+    B.build()
+    import paper_2112_10913_gb300 as cg
+    from paper_2112_10913_gb300 import graphgen as gg
+
+    g = gg.config3_chung_lu()
+    dev = torch.device("cuda")
+    off = torch.from_numpy(g.off.view(np.int64)).to(dev)
+    cols = torch.from_numpy(g.cols.view(np.int32)).to(dev)
+    ws = cg.alloc_workspace(g.n, g.arcs, 1, device=dev)
+    rank = torch.empty(g.n, dtype=torch.int32, device=dev)
+    dag_off = torch.empty(g.n + 1, dtype=torch.int64, device=dev)
+    dag_cols = torch.empty(g.arcs // 2, dtype=torch.int32, device=dev)
+
+    def order_dag():
+        cg.citron_order(g.n, off, rank, None, ws)
+        return cg.citron_build_dag(g.n, off, cols, rank, dag_off, dag_cols, ws)
+
+    mx = order_dag()
+    if cg.citron_workspace_bytes(g.n, g.arcs, mx) > ws.numel():
+        ws = cg.alloc_workspace(g.n, g.arcs, mx, device=dev)
+    t_order = _events_ms(order_dag)
+    per_k = {}
+    for k in range(5, 10):
+        pr = torch.zeros(g.n, dtype=torch.int64, device=dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        c = cg.citron_count(g.n, dag_off, dag_cols, k, ws, mx, pr)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        p = np.sort(pr.cpu().numpy().view(np.uint64).astype(np.float64))[::-1]
+        per_k[str(k)] = dict(count=c, count_ms=ms, order_ms=t_order,
+                             edges_per_s=g.m / ((ms + t_order) * 1e-3),
+                             top_root_share=float(p[0] / max(p.sum(), 1)),
+                             top100_share=float(p[:100].sum() / max(p.sum(), 1)))
+        if ms > 60000:
+            break
+    ks = list(per_k)
+    tot = sum(per_k[k]["count_ms"] + t_order for k in ks)
+    return {
+        "metric": "order+count edges/s on the Chung-Lu 4M graph (exact)",
+        "value": g.m * len(ks) / (tot * 1e-3), "unit": "edges/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": tot, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32/u64 (exact integer)", "data": "synthetic (seeded Chung-Lu)",
+        "config": {"workload": "chunglu-4M beta=2.1 avg30 cap20000 + 50 planted cliques", "n": g.n,
+                   "m_undirected": g.m, "max_outdeg": mx, "ks": [int(k) for k in ks]},
+        "per_k": per_k,
     }
 
 
@@ -494,6 +670,12 @@ def main():
         line = run_batch(args)
     elif args.workload == "serve":
         line = run_serve(args)
+    elif args.workload == "orderings":
+        line = run_orderings(args)
+    elif args.workload == "list":
+        line = run_list(args)
+    elif args.workload == "chunglu":
+        line = run_chunglu(args)
     elif args.impl == "reference":
         line = run_reference(args, ks)
     else:

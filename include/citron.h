@@ -82,6 +82,28 @@ citron_status citron_order(uint32_t n, const uint64_t *d_off, uint32_t *d_rank, 
                            void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * citron_core_order -- the core ordering of Algorithm OrdCore (Sec. III), computed in
+ * synchronous peeling rounds: each round raises a level to the smallest remaining degree (it
+ * never falls) and removes, together, every remaining vertex whose remaining degree is at most
+ * the level; then their neighbours' remaining degrees drop.  The order is (removal round, id).
+ * As with the paper's one-vertex-at-a-time removal, orienting edges from earlier to later vertices
+ * gives a DAG whose maximum out-degree is the degeneracy (the smallest possible, Sec. III and
+ * Table II); the order itself can differ from the sequential one.
+ *   d_off[n+1], d_cols[arcs] (device): the undirected graph, as for citron_build_dag.
+ *   d_rank[u] (device, n entries, written) = position of u; d_perm (optional) = the inverse.
+ *   h_degeneracy, h_rounds (host, optional): the final level (the degeneracy) and the number of
+ *   rounds.
+ * One cooperative kernel runs all rounds (grid barriers with a bounded wait; a wait that gives
+ * up returns CITRON_E_TIMEOUT), then a radix sort by round.  Synchronises `stream`.  Returns
+ * CITRON_E_UNSUPPORTED on a device without cooperative launch.  Pass the rank to
+ * citron_build_dag for the core-ordered DAG.
+ */
+citron_status citron_core_order(uint32_t n, uint64_t arcs, const uint64_t *d_off,
+                                const uint32_t *d_cols, uint32_t *d_rank, uint32_t *d_perm,
+                                uint32_t *h_degeneracy, uint32_t *h_rounds, void *ws,
+                                size_t ws_bytes, void *stream);
+
+/*
  * citron_build_dag -- directionalise the graph (Sec. II) into a DAG in CSR form.
  *   d_rank == NULL: Algorithm GenOrdering (Sec. IV): the arc u->v is kept iff
  *       d(u) < d(v) or (d(u) == d(v) and u < v); vertex ids are unchanged and each row keeps the
@@ -116,6 +138,24 @@ citron_status citron_build_dag(uint32_t n, uint64_t arcs, const uint64_t *d_off,
 citron_status citron_count(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
                            uint32_t k, uint32_t max_outdeg, uint64_t *h_count,
                            uint64_t *d_per_root, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * citron_list -- write out every k-clique instead of counting it (the extension of the counting
+ * recursion that Sec. VIII describes).  Each clique is one row of k uint32 ids in recursion
+ * order: its first vertex in the DAG order, then the vertex of its edge task, then the vertices
+ * chosen level by level (ascending DAG ids for a DAG relabelled to ranks).
+ *   d_map (device, optional): ids are written as d_map[id] (pass the inverse rank, i.e. the
+ *       d_perm of citron_order, to get input vertex ids from a relabelled DAG); NULL writes DAG ids.
+ *   d_out (device, capacity * k uint32, caller-allocated): the rows, in no particular order.
+ *   capacity: rows d_out can hold; 0 (with d_out NULL) only counts.
+ *   *h_total (host, required): the number of k-cliques.  When *h_total > capacity, only
+ *       `capacity` rows were written, an unspecified subset: call again with a larger buffer.
+ * Limits: k <= CITRON_MAX_K; a DAG row longer than 1024 returns CITRON_E_UNSUPPORTED (the rows
+ * of a root's local subgraph are held in shared memory).  Synchronises `stream`.
+ */
+citron_status citron_list(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
+                          uint32_t k, const uint32_t *d_map, uint32_t *d_out, uint64_t capacity,
+                          uint64_t *h_total, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * citron_count_ex -- citron_count with options: the internal path thresholds (for tests that must

@@ -33,9 +33,11 @@ EXPORTS = (
     "citron_workspace_bytes",
     "citron_validate",
     "citron_order",
+    "citron_core_order",
     "citron_build_dag",
     "citron_count",
     "citron_count_ex",
+    "citron_list",
     "citron_kernel_launches",
     "citron_host_buffer_bytes",
     "citron_count_host",
@@ -94,12 +96,16 @@ def lib() -> ctypes.CDLL:
     L.citron_validate.restype = i32
     L.citron_order.argtypes = [u32, vp, vp, vp, vp, sz, vp]
     L.citron_order.restype = i32
+    L.citron_core_order.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.citron_core_order.restype = i32
     L.citron_build_dag.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.citron_build_dag.restype = i32
     L.citron_count.argtypes = [u32, vp, vp, u32, u32, vp, vp, vp, sz, vp]
     L.citron_count.restype = i32
     L.citron_count_ex.argtypes = [u32, vp, vp, u32, u32, vp, vp, vp, sz, vp]
     L.citron_count_ex.restype = i32
+    L.citron_list.argtypes = [u32, vp, vp, u32, vp, vp, u64, vp, vp, sz, vp]
+    L.citron_list.restype = i32
     L.citron_kernel_launches.argtypes = []
     L.citron_kernel_launches.restype = u64
     L.citron_host_buffer_bytes.argtypes = [u32, u64]
@@ -174,6 +180,15 @@ def citron_order(n: int, off, rank, perm=None, ws=None, stream=None):
                               _stream(stream)), "citron_order")
 
 
+def citron_core_order(n: int, off, cols, rank, perm=None, ws=None, stream=None) -> tuple[int, int]:
+    """Core ordering by synchronous peeling rounds; returns (degeneracy, rounds)."""
+    level, rounds = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    _check(lib().citron_core_order(n, int(cols.numel()), _dptr(off), _dptr(cols), _dptr(rank),
+                                   _dptr(perm), ctypes.byref(level), ctypes.byref(rounds),
+                                   _dptr(ws), _nbytes(ws), _stream(stream)), "citron_core_order")
+    return int(level.value), int(rounds.value)
+
+
 def citron_build_dag(n: int, off, cols, rank, dag_off, dag_cols, ws, stream=None,
                      want_max_outdeg: bool = True):
     mx = ctypes.c_uint32(0)
@@ -230,6 +245,19 @@ def citron_workspace_status(ws, stream=None):
     _check(lib().citron_workspace_status(_dptr(ws), _stream(stream)), "citron_workspace_status")
 
 
+def citron_list(n: int, dag_off, dag_cols, k: int, ws, out=None, capacity: int | None = None,
+                id_map=None, stream=None) -> int:
+    """Write the k-cliques as rows of `out` (a CUDA int32 tensor of shape (capacity, k)); returns
+    the number of k-cliques (only min(total, capacity) rows are written)."""
+    total = ctypes.c_uint64(0)
+    if capacity is None:
+        capacity = 0 if out is None else int(out.shape[0])
+    _check(lib().citron_list(n, _dptr(dag_off), _dptr(dag_cols), k, _dptr(id_map), _dptr(out),
+                             capacity, ctypes.byref(total), _dptr(ws), _nbytes(ws), _stream(stream)),
+           "citron_list")
+    return int(total.value)
+
+
 def citron_kernel_launches() -> int:
     return int(lib().citron_kernel_launches())
 
@@ -265,10 +293,12 @@ class DeviceGraph:
     """A CSR graph uploaded once, with its degree ordering and DAG built on the device.
 
     ``relabel=True`` (default) builds the DAG in rank space from citron_order's ranks;
-    ``relabel=False`` builds the paper's GenOrdering DAG in the input's vertex ids.
+    ``relabel=False`` builds the paper's GenOrdering DAG in the input's vertex ids;
+    ``ordering="core"`` ranks by citron_core_order instead (relabelled DAG).
     """
 
-    def __init__(self, g, relabel: bool = True, device="cuda", stream=None, rank=None):
+    def __init__(self, g, relabel: bool = True, device="cuda", stream=None, rank=None,
+                 ordering: str = "degree"):
         import torch
 
         self.n = g.n
@@ -278,8 +308,15 @@ class DeviceGraph:
         self.cols = torch.from_numpy(np.ascontiguousarray(g.cols).view(np.int32)).to(dev)
         self.ws = alloc_workspace(self.n, self.arcs, 1, device=dev)
         self.rank = None
+        self.degeneracy = self.rounds = None
+        if ordering not in ("degree", "core"):
+            raise ValueError("ordering is 'degree' or 'core'")
         if rank is not None:
             self.rank = torch.as_tensor(np.asarray(rank, dtype=np.uint32).view(np.int32), device=dev)
+        elif ordering == "core":
+            self.rank = torch.empty(max(1, self.n), dtype=torch.int32, device=dev)
+            self.degeneracy, self.rounds = citron_core_order(self.n, self.off, self.cols, self.rank,
+                                                             None, self.ws, stream)
         elif relabel:
             self.rank = torch.empty(max(1, self.n), dtype=torch.int32, device=dev)
             citron_order(self.n, self.off, self.rank, None, self.ws, stream)
@@ -297,6 +334,21 @@ class DeviceGraph:
                                    per_root, stream, **tuned)[0]
         return citron_count(self.n, self.dag_off, self.dag_cols, k, self.ws, self.max_outdeg,
                             per_root, stream)
+
+    def list(self, k: int, input_ids: bool = True, stream=None) -> np.ndarray:
+        """Every k-clique as a row of k vertex ids (input ids by default), shape (K_k, k)."""
+        import torch
+
+        total = citron_list(self.n, self.dag_off, self.dag_cols, k, self.ws, None, 0, None, stream)
+        out = torch.empty((max(1, total), k), dtype=torch.int32, device=self.dag_off.device)
+        id_map = None
+        if input_ids and self.rank is not None:
+            id_map = torch.empty_like(self.rank)
+            id_map[self.rank.long()] = torch.arange(self.n, dtype=torch.int32, device=self.rank.device)
+        got = citron_list(self.n, self.dag_off, self.dag_cols, k, self.ws, out, total, id_map, stream)
+        if got != total:
+            raise RuntimeError("clique count changed between the sizing and the listing call")
+        return out[:total].cpu().numpy().view(np.uint32)
 
     def dag_numpy(self):
         off = self.dag_off.cpu().numpy().view(np.uint64)

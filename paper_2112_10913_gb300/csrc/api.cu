@@ -17,6 +17,16 @@ cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, con
                              const uint32_t *rank, uint64_t *dag_off, uint32_t *dag_cols,
                              uint32_t *d_max_outdeg, uint32_t *err, Carver &c, cudaStream_t st,
                              int num_sms);
+size_t core_ws_bytes(uint32_t n);
+size_t list_ws_bytes();
+cudaError_t run_list(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
+                     const uint32_t *map, uint32_t *out, unsigned long long capacity,
+                     unsigned long long *h_total, bool *too_wide, uint32_t *err, Carver &c,
+                     cudaStream_t st, int num_sms);
+cudaError_t launch_core_order(uint32_t n, uint64_t arcs, const uint64_t *off, const uint32_t *cols,
+                              uint32_t *rank, uint32_t *perm, uint32_t *h_level,
+                              uint32_t *h_rounds, uint32_t *err, Carver &c, cudaStream_t st,
+                              int num_sms);
 cudaError_t launch_validate(uint32_t n, uint64_t arcs, const uint64_t *off, const uint32_t *cols,
                             uint32_t *bad, cudaStream_t st, int num_sms);
 size_t count_ws_bytes(uint32_t n, uint32_t max_outdeg, int num_sms);
@@ -151,6 +161,8 @@ size_t citron_workspace_bytes(uint32_t n, uint64_t arcs, uint32_t max_outdeg)
     size_t need = order_ws_bytes(n);
     size_t d = dag_ws_bytes(n, arcs);
     if (d > need) need = d;
+    d = core_ws_bytes(n);
+    if (d > need) need = d;
     size_t c = count_ws_bytes(n, max_outdeg, sm_count()) + (((size_t)n + 1) * 4 + 255) / 256 * 256;
     if (c > need) need = c;
     return kHeader + need;
@@ -181,6 +193,26 @@ citron_status citron_order(uint32_t n, const uint64_t *d_off, uint32_t *d_rank, 
     if (!ws_ok(ws, ws_bytes, kHeader + order_ws_bytes(n))) return CITRON_E_WORKSPACE;
     Carver c((char *)ws + kHeader, ws_bytes - kHeader);
     return from_cuda(launch_order(n, d_off, d_rank, d_perm, c, (cudaStream_t)stream));
+}
+
+citron_status citron_core_order(uint32_t n, uint64_t arcs, const uint64_t *d_off,
+                                const uint32_t *d_cols, uint32_t *d_rank, uint32_t *d_perm,
+                                uint32_t *h_degeneracy, uint32_t *h_rounds, void *ws,
+                                size_t ws_bytes, void *stream)
+{
+    if (n == 0xffffffffu || !d_off || (n && !d_rank) || (arcs && !d_cols) || (arcs & 1))
+        return CITRON_E_INVALID;
+    if (!ws_ok(ws, ws_bytes, kHeader + core_ws_bytes(n))) return CITRON_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c((char *)ws + kHeader, ws_bytes - kHeader);
+    cudaError_t e = launch_core_order(n, arcs, d_off, d_cols, d_rank, d_perm, h_degeneracy, h_rounds,
+                                      err_word(ws), c, s, sm_count());
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        return CITRON_E_UNSUPPORTED;
+    }
+    if (e) return from_cuda(e);
+    return finish_sync(ws, s, CITRON_OK);
 }
 
 citron_status citron_build_dag(uint32_t n, uint64_t arcs, const uint64_t *d_off,
@@ -248,6 +280,27 @@ citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint3
     if (st == CITRON_OK) *h_count = result;
     opts->work_ops = run.work;
     for (int i = 0; i < 3; i++) opts->kernel_ms[i] = run.kernel_ms[i];
+    return st;
+}
+
+citron_status citron_list(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,
+                          uint32_t k, const uint32_t *d_map, uint32_t *d_out, uint64_t capacity,
+                          uint64_t *h_total, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!h_total || !d_dag_off || n == 0xffffffffu || k == 0 || (capacity && !d_out) ||
+        (k >= 2 && n && !d_dag_cols))
+        return CITRON_E_INVALID;
+    if (k > CITRON_MAX_K) return CITRON_E_UNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, kHeader + list_ws_bytes())) return CITRON_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c((char *)ws + kHeader, ws_bytes - kHeader);
+    unsigned long long total = 0;
+    bool too_wide = false;
+    cudaError_t e = run_list(n, d_dag_off, d_dag_cols, k, d_map, d_out, capacity, &total, &too_wide,
+                             err_word(ws), c, s, sm_count());
+    if (e) return from_cuda(e);
+    citron_status st = finish_sync(ws, s, too_wide ? CITRON_E_UNSUPPORTED : CITRON_OK);
+    if (st == CITRON_OK) *h_total = total;
     return st;
 }
 

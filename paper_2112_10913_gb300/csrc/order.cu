@@ -651,8 +651,10 @@ static int radix_passes(uint32_t n)
     return bits <= 8 ? 1 : (bits + 7) / 8;
 }
 
-cudaError_t launch_order(uint32_t n, const uint64_t *off, uint32_t *rank, uint32_t *perm,
-                         Carver &c, cudaStream_t st)
+// Stable LSD sort of the ids 0..n-1 by a key: the degree (keys0 == NULL) or keys0[id].  Writes
+// rank[id] = position and, when perm != NULL, perm[position] = id.  `passes` 8-bit digits.
+static cudaError_t sort_ids(uint32_t n, const uint64_t *off, const uint32_t *keys0, int passes,
+                            uint32_t *rank, uint32_t *perm, Carver &c, cudaStream_t st)
 {
     const uint32_t nb = (n + kRsTile - 1) / kRsTile;
     uint32_t *keys[2] = {c.take<uint32_t>(n), c.take<uint32_t>(n)};
@@ -660,8 +662,7 @@ cudaError_t launch_order(uint32_t n, const uint64_t *off, uint32_t *rank, uint32
     uint32_t *hist = c.take<uint32_t>((size_t)256 * (nb + 1));
     if (!c.ok) return cudaErrorMemoryAllocation;
     if (n == 0) return cudaSuccess;
-    const int passes = radix_passes(n);
-    const uint32_t *kin = nullptr, *vin = nullptr;
+    const uint32_t *kin = keys0, *vin = nullptr;
     for (int p = 0; p < passes; p++) {
         const bool last = p == passes - 1;
         k_radix_hist<<<nb, kRsThreads, 0, st>>>(off, kin, n, 8 * p, hist, nb);
@@ -675,6 +676,19 @@ cudaError_t launch_order(uint32_t n, const uint64_t *off, uint32_t *rank, uint32
         vin = vout;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_order(uint32_t n, const uint64_t *off, uint32_t *rank, uint32_t *perm,
+                         Carver &c, cudaStream_t st)
+{
+    return sort_ids(n, off, nullptr, radix_passes(n), rank, perm, c, st);
+}
+
+// Ranks by (key, id) for keys below key_bound (the core ordering's removal rounds).
+cudaError_t launch_rank_by_key(uint32_t n, const uint32_t *keys, uint32_t key_bound, uint32_t *rank,
+                               uint32_t *perm, Carver &c, cudaStream_t st)
+{
+    return sort_ids(n, nullptr, keys, radix_passes(key_bound ? key_bound : 1), rank, perm, c, st);
 }
 
 size_t dag_ws_bytes(uint32_t n, uint64_t arcs)

@@ -68,6 +68,11 @@ def test_argument_checks_need_no_gpu(built):
                               ctypes.c_void_p(1), null, null, 0, null) == 1
     # n = 2^32 - 1 is reserved
     assert L.citron_validate(0xFFFFFFFF, 0, ctypes.c_void_p(1), null, null, null, 0, null) == 1
+    # core ordering: odd arc count, missing rank, missing workspace
+    one = ctypes.c_void_p(1)
+    assert L.citron_core_order(4, 3, one, one, one, null, null, null, null, 0, null) == 1
+    assert L.citron_core_order(4, 4, one, one, null, null, null, null, null, 0, null) == 1
+    assert L.citron_core_order(4, 4, one, one, one, null, null, null, null, 0, null) == 2
 
 
 def test_workspace_size_grows_with_graph(built):

@@ -35,6 +35,19 @@ def test_dag_bytes_full(gpu, oracle_lib, rmat20, dev):
     assert np.array_equal(goff0, off0) and np.array_equal(gcols0, cols0)
 
 
+def test_core_order_full(gpu, oracle_lib, rmat20, dev):
+    """Core ordering at full size: rank, degeneracy and rounds equal the oracle's; the core DAG's
+    maximum out-degree is the degeneracy, below the degree ordering's; counts agree."""
+    g = rmat20
+    core = gpu.DeviceGraph(g, ordering="core")
+    want, level, rounds = oracle_lib.core_rank_rounds(g.off, g.cols, g.n)
+    assert np.array_equal(core.rank.cpu().numpy().view(np.uint32), want)
+    assert (core.degeneracy, core.rounds) == (level, rounds)
+    assert core.max_outdeg == level < dev.max_outdeg
+    for k in (3, 4, 5):
+        assert core.count(k) == dev.count(k)
+
+
 def test_triangles_full(oracle_lib, dev):
     off, cols = dev.dag_numpy()
     assert dev.count(3) == oracle_lib.count(off, cols, dev.n, 3)
