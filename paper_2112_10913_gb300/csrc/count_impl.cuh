@@ -135,6 +135,7 @@ struct WarpCtx {
     uint32_t *mv;    // compress masks: 5 per candidate word, then the member prefix per word
     uint32_t *mbuf;  // compact rows, 4 words each (16-byte aligned); aliases lbuf
     uint32_t compact_max;  // largest candidate set re-encoded compactly (0 or 128)
+    uint32_t compact3_max; // same for the R = 3 level, which also takes packed 5- and 6-word rows
 };
 
 // Number of DAG arcs inside the lane's own candidate set lb (words [lo, hi)): the penultimate
@@ -308,6 +309,109 @@ __device__ __forceinline__ void build_compact(const WarpCtx &x, uint32_t s, int 
     __syncwarp();
 }
 
+// Packed triangular compact rows for R = 3 sets of 129..192 members (CW = 5 or 6 words): the row
+// of member i holds only its words q = i/32 .. CW-1 (the words below are zero in an
+// upper-triangular sub-DAG), so 192 rows take 672 words instead of 1152 and fit the warp's
+// scratch.  Rows of the members of word q start at packed_base(q) and are (CW - q) words long.
+template <int CW>
+__host__ __device__ constexpr uint32_t packed_base(int q)
+{
+    return q <= 0 ? 0u : packed_base<CW>(q - 1) + 32u * (uint32_t)(CW - (q - 1));
+}
+
+__host__ __device__ constexpr uint32_t packed_words(int cw) { return 16u * (uint32_t)(cw * (cw + 1)); }
+
+template <int CW>
+__device__ __forceinline__ void build_packed(const WarpCtx &x, uint32_t s, int clo, int chi, int lane)
+{
+    {
+        const uint32_t m = (lane < chi && lane >= clo) ? x.cbuf[lane] : 0u;
+        uint32_t mv[5];
+        compress_masks(m, mv);
+        const uint32_t pc = __popc(m);
+        const uint32_t pre = warp_incl_scan(pc) - pc;
+#pragma unroll
+        for (int i = 0; i < 5; i++) x.mv[i * 32 + lane] = mv[i];
+        x.mv[160 + lane] = pre;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < CW; q++) {
+        const uint32_t i0 = (uint32_t)q * 32;
+        if (i0 >= s) break;
+        const uint32_t i = i0 + lane;
+        const bool act = i < s;
+        const uint32_t ei = act ? x.elem[i] : x.elem[i0];
+        const uint32_t *row = x.rows + ei * x.RS;
+        uint32_t o[CW];
+#pragma unroll
+        for (int t = 0; t < CW; t++) o[t] = 0;
+        for (int w = (int)(x.elem[i0] >> 5); w < chi; w++) {
+            const uint32_t m = x.cbuf[w];
+            if (!m) continue;
+            uint32_t mv[5];
+#pragma unroll
+            for (int t = 0; t < 5; t++) mv[t] = x.mv[t * 32 + w];
+            const uint32_t pre = x.mv[160 + w];
+            const uint32_t piece = compress_with(row[w], m, mv);
+            const uint32_t qq = pre >> 5, sh = pre & 31;
+            const uint32_t lo = piece << sh, hi = sh ? (piece >> (32 - sh)) : 0u;
+#pragma unroll
+            for (int t = 0; t < CW; t++) o[t] |= (qq == (uint32_t)t ? lo : 0u) | (qq + 1 == (uint32_t)t ? hi : 0u);
+        }
+        if (act) {
+            uint32_t *dst = x.mbuf + packed_base<CW>(q) + (uint32_t)lane * (CW - q);
+#pragma unroll
+            for (int t = q; t < CW; t++) dst[t - q] = o[t];
+        }
+    }
+    __syncwarp();
+}
+
+// Arcs inside the lane's set D (CW words; zero below word FROMQ) on packed rows.
+template <int CW, bool WORK, int Q2>
+__device__ __forceinline__ uint32_t packed_leaf(const uint32_t *P, const uint32_t (&D)[CW],
+                                                unsigned long long &work)
+{
+    uint32_t s = 0;
+    if constexpr (Q2 < CW) {
+        uint32_t y = D[Q2];
+        if (WORK) work += (unsigned long long)__popc(y) * (CW - Q2);
+        while (y) {
+            const uint32_t jl = (uint32_t)__ffs(y) - 1;
+            y &= y - 1;
+            const uint32_t *rj = P + packed_base<CW>(Q2) + jl * (CW - Q2);
+#pragma unroll
+            for (int w = Q2; w < CW; w++) s += __popc(D[w] & rj[w - Q2]);
+        }
+        s += packed_leaf<CW, WORK, Q2 + 1>(P, D, work);
+    }
+    return s;
+}
+
+// Triangles of a dense compact set of s members (members 0..s-1) on packed rows: lane l takes
+// member 32q + l of each word q, forms D = C ∧ row and adds the arcs inside D.
+template <int CW, bool WORK, int Q>
+__device__ __forceinline__ void packed_r3(const uint32_t *P, uint32_t s_members, int lane,
+                                          uint32_t &s, unsigned long long &work)
+{
+    if constexpr (Q < CW) {
+        const uint32_t m = (uint32_t)Q * 32 + lane;
+        if (m < s_members) {
+            const uint32_t *rm = P + packed_base<CW>(Q) + (uint32_t)lane * (CW - Q);
+            uint32_t D[CW];
+#pragma unroll
+            for (int w = 0; w < CW; w++) {
+                const uint32_t cw = (uint32_t)w * 32 >= s_members ? 0u
+                                    : (s_members >= (uint32_t)w * 32 + 32 ? kFull : ((1u << (s_members - w * 32)) - 1));
+                D[w] = w < Q ? 0u : (cw & rm[w - Q]);
+            }
+            s += packed_leaf<CW, WORK, Q>(P, D, work);
+        }
+        packed_r3<CW, WORK, Q + 1>(P, s_members, lane, s, work);
+    }
+}
+
 // Sum of popc(a[w] & b[w]) over words w in [FROM, CW).
 template <int CW, int FROM>
 __device__ __forceinline__ uint32_t popc_and(const uint32_t (&a)[CW], const uint4 &b)
@@ -361,6 +465,53 @@ __device__ __forceinline__ void cdfs_word(const uint4 *M, const uint32_t (&C)[CW
     }
 }
 
+// Triangles (R = 3) inside a compact set C whose members are scattered over its CW words (a set
+// derived from a wider one, C ∧ row).  Member m_r (in index order) goes to lane r mod 32, so that
+// every lane of a round holds a member (dealing by bit position would leave the lanes of the
+// absent members idle); lane r forms D = C ∧ row(m_r) and adds the arcs inside D.
+template <int CW, bool TRI, bool WORK>
+__device__ __forceinline__ void cdfs3_dealt(const WarpCtx &x, const uint32_t (&C)[CW], int lane,
+                                            unsigned long long &acc, unsigned long long &work)
+{
+    const uint4 *M = reinterpret_cast<const uint4 *>(x.mbuf);
+    uint32_t total = 0;
+#pragma unroll
+    for (int q = 0; q < CW; q++) {
+        if ((C[q] >> lane) & 1) x.elem[total + __popc(C[q] & lanemask_lt())] = (uint16_t)(q * 32 + lane);
+        total += __popc(C[q]);
+    }
+    __syncwarp();
+    uint32_t s = 0;
+    for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+        if (r0 + lane < total) {
+            const uint32_t m = x.elem[r0 + lane];
+            const uint4 mi = M[m];
+            uint32_t D[CW];
+            D[0] = C[0] & mi.x;
+            if (CW > 1) D[1] = C[1] & mi.y;
+            if (CW > 2) D[2] = C[2] & mi.z;
+            if (CW > 3) D[3] = C[3] & mi.w;
+#pragma unroll
+            for (int q2 = 0; q2 < CW; q2++) {
+                uint32_t y = D[q2];  // zero below the member's own word when TRI
+                if (WORK) work += (unsigned long long)__popc(y) * (TRI ? CW - q2 : CW);
+                while (y) {
+                    const uint32_t j = (uint32_t)(q2 << 5) + __ffs(y) - 1;
+                    y &= y - 1;
+                    const uint4 mj = M[j];
+                    if (!TRI) s += popc_and<CW, 0>(D, mj);
+                    else if (q2 == 0) s += popc_and<CW, 0>(D, mj);
+                    else if (q2 == 1) s += popc_and<CW, 1>(D, mj);
+                    else if (q2 == 2) s += popc_and<CW, 2>(D, mj);
+                    else s += popc_and<CW, 3>(D, mj);
+                }
+            }
+        }
+    }
+    acc += s;
+    __syncwarp();
+}
+
 // R-cliques inside the compact set C (CW words, the same on every lane); rows in mbuf.
 template <int R, int CW, bool TRI, bool WORK>
 __device__ __forceinline__ void cdfs(const WarpCtx &x, const uint32_t (&C)[CW], int lane,
@@ -407,7 +558,10 @@ __device__ __forceinline__ void cdfs(const WarpCtx &x, const uint32_t (&C)[CW], 
 #pragma unroll
             for (int t = 0; t < CW; t++) cnt += __popc(C2[t]);
             if (WORK && lane == 0) work += CW;
-            if (cnt >= R - 1) cdfs<R - 1, CW, TRI, WORK>(x, C2, lane, acc, work);
+            if (cnt >= R - 1) {
+                if constexpr (R == 4) cdfs3_dealt<CW, TRI, WORK>(x, C2, lane, acc, work);
+                else cdfs<R - 1, CW, TRI, WORK>(x, C2, lane, acc, work);
+            }
         }
     }
 }
@@ -438,6 +592,16 @@ __device__ __forceinline__ void compact_entry(const WarpCtx &x, uint32_t c, int 
         else if (s <= 64) cdfs_all<R, 2, true, WORK>(x, s, lane, acc, work);
         else if (s <= 96) cdfs_all<R, 3, true, WORK>(x, s, lane, acc, work);
         else cdfs_all<R, 4, true, WORK>(x, s, lane, acc, work);
+    } else if constexpr (R == 3) {
+        uint32_t t = 0;
+        if (s <= 160) {
+            build_packed<5>(x, s, clo, chi, lane);
+            packed_r3<5, WORK, 0>(x.mbuf, s, lane, t, work);
+        } else {
+            build_packed<6>(x, s, clo, chi, lane);
+            packed_r3<6, WORK, 0>(x.mbuf, s, lane, t, work);
+        }
+        acc += t;
     }
     __syncwarp();
 }
@@ -454,7 +618,7 @@ __device__ __forceinline__ void warp_dfs(const WarpCtx &x, uint32_t c, int lane,
                                          unsigned long long &acc, unsigned long long &work)
 {
     if constexpr (R >= 3) {
-        if (x.tri && __reduce_add_sync(kFull, __popc(c)) <= x.compact_max) {
+        if (x.tri && __reduce_add_sync(kFull, __popc(c)) <= (R == 3 ? x.compact3_max : x.compact_max)) {
             compact_entry<R, WORK>(x, c, lane, acc, work);
             return;
         }
@@ -543,10 +707,10 @@ __device__ __forceinline__ void warp_dfs(const WarpCtx &x, uint32_t c, int lane,
 
 // Shared-memory words one warp needs for roots of out-degree <= dcap (dcap multiple of 32).
 // Layout: elem (dcap uint16) | cbuf (32) | compress masks + prefixes (192) | lbuf/mbuf, where
-// mbuf holds compact_max rows of 4 words.
+// mbuf holds compact_max rows of 4 words or the packed rows of an R = 3 set of up to 192 members.
 __host__ __device__ __forceinline__ uint32_t warp_scratch_words(uint32_t dcap, uint32_t compact_max)
 {
-    const uint32_t m = compact_max * 4;
+    const uint32_t m = compact_max ? (compact_max * 4 > packed_words(6) ? compact_max * 4 : packed_words(6)) : 0u;
     return dcap / 2 + 32 + 192 + (dcap > m ? dcap : m);
 }
 
@@ -575,6 +739,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     x.lbuf = wscr + dcap / 2 + 32 + 192;
     x.mbuf = x.lbuf;
     x.compact_max = compact_max;
+    x.compact3_max = compact_max ? 192u : 0u;
     const uint32_t nlist = st->n_mid;
     unsigned long long block_total = 0;  // meaningful in thread 0
     for (;;) {
