@@ -309,6 +309,22 @@ __device__ __forceinline__ void build_compact(const WarpCtx &x, uint32_t s, int 
     __syncwarp();
 }
 
+// Iteration mask of a leaf set: its members except the highest one.  In the triangular layout a
+// member's row has no bits at or below its own index, so the highest member of a set adds no
+// arc inside it and is not visited.
+template <int CW>
+__device__ __forceinline__ void drop_top(uint32_t (&Y)[CW])
+{
+    bool done = false;
+#pragma unroll
+    for (int q = CW - 1; q >= 0; q--) {
+        if (!done && Y[q]) {
+            Y[q] &= ~(0x80000000u >> __clz(Y[q]));
+            done = true;
+        }
+    }
+}
+
 // Packed triangular compact rows for R = 3 sets of 129..192 members (CW = 5 or 6 words): the row
 // of member i holds only its words q = i/32 .. CW-1 (the words below are zero in an
 // upper-triangular sub-DAG), so 192 rows take 672 words instead of 1152 and fit the warp's
@@ -368,23 +384,24 @@ __device__ __forceinline__ void build_packed(const WarpCtx &x, uint32_t s, int c
     __syncwarp();
 }
 
-// Arcs inside the lane's set D (CW words; zero below word FROMQ) on packed rows.
+// Arcs inside the lane's set D (CW words; zero below word Q2) on packed rows; Y = the members
+// to visit (D without its highest member).
 template <int CW, bool WORK, int Q2>
 __device__ __forceinline__ uint32_t packed_leaf(const uint32_t *P, const uint32_t (&D)[CW],
-                                                unsigned long long &work)
+                                                const uint32_t (&Y)[CW], unsigned long long &work)
 {
     uint32_t s = 0;
     if constexpr (Q2 < CW) {
-        uint32_t y = D[Q2];
+        uint32_t y = Y[Q2];
         if (WORK) work += (unsigned long long)__popc(y) * (CW - Q2);
         while (y) {
-            const uint32_t jl = (uint32_t)__ffs(y) - 1;
-            y &= y - 1;
+            const uint32_t jl = 31u - __clz(y);
+            y ^= 1u << jl;
             const uint32_t *rj = P + packed_base<CW>(Q2) + jl * (CW - Q2);
 #pragma unroll
             for (int w = Q2; w < CW; w++) s += __popc(D[w] & rj[w - Q2]);
         }
-        s += packed_leaf<CW, WORK, Q2 + 1>(P, D, work);
+        s += packed_leaf<CW, WORK, Q2 + 1>(P, D, Y, work);
     }
     return s;
 }
@@ -406,7 +423,11 @@ __device__ __forceinline__ void packed_r3(const uint32_t *P, uint32_t s_members,
                                     : (s_members >= (uint32_t)w * 32 + 32 ? kFull : ((1u << (s_members - w * 32)) - 1));
                 D[w] = w < Q ? 0u : (cw & rm[w - Q]);
             }
-            s += packed_leaf<CW, WORK, Q>(P, D, work);
+            uint32_t Y[CW];
+#pragma unroll
+            for (int w = 0; w < CW; w++) Y[w] = D[w];
+            drop_top<CW>(Y);
+            s += packed_leaf<CW, WORK, Q>(P, D, Y, work);
         }
         packed_r3<CW, WORK, Q + 1>(P, s_members, lane, s, work);
     }
@@ -444,13 +465,18 @@ __device__ __forceinline__ void cdfs_word(const uint4 *M, const uint32_t (&C)[CW
                 if (CW > 1) D[1] = C[1] & mi.y;
                 if (CW > 2) D[2] = C[2] & mi.z;
                 if (CW > 3) D[3] = C[3] & mi.w;
+                uint32_t Y[CW];
+#pragma unroll
+                for (int w = 0; w < CW; w++) Y[w] = D[w];
+                if (TRI) drop_top<CW>(Y);
 #pragma unroll
                 for (int q2 = TRI ? Q : 0; q2 < CW; q2++) {
-                    uint32_t y = D[q2];
+                    uint32_t y = Y[q2];
                     if (WORK) work += (unsigned long long)__popc(y) * (TRI ? CW - q2 : CW);
                     while (y) {
-                        const uint32_t j = (uint32_t)(q2 << 5) + __ffs(y) - 1;
-                        y &= y - 1;
+                        const uint32_t b = 31u - __clz(y);
+                        y ^= 1u << b;
+                        const uint32_t j = (uint32_t)(q2 << 5) + b;
                         const uint4 mj = M[j];
                         if (!TRI) s += popc_and<CW, 0>(D, mj);
                         else if (q2 == 0) s += popc_and<CW, 0>(D, mj);
@@ -491,13 +517,18 @@ __device__ __forceinline__ void cdfs3_dealt(const WarpCtx &x, const uint32_t (&C
             if (CW > 1) D[1] = C[1] & mi.y;
             if (CW > 2) D[2] = C[2] & mi.z;
             if (CW > 3) D[3] = C[3] & mi.w;
+            uint32_t Y[CW];
+#pragma unroll
+            for (int w = 0; w < CW; w++) Y[w] = D[w];
+            if (TRI) drop_top<CW>(Y);
 #pragma unroll
             for (int q2 = 0; q2 < CW; q2++) {
-                uint32_t y = D[q2];  // zero below the member's own word when TRI
+                uint32_t y = Y[q2];  // zero below the member's own word when TRI
                 if (WORK) work += (unsigned long long)__popc(y) * (TRI ? CW - q2 : CW);
                 while (y) {
-                    const uint32_t j = (uint32_t)(q2 << 5) + __ffs(y) - 1;
-                    y &= y - 1;
+                    const uint32_t b = 31u - __clz(y);
+                    y ^= 1u << b;
+                    const uint32_t j = (uint32_t)(q2 << 5) + b;
                     const uint4 mj = M[j];
                     if (!TRI) s += popc_and<CW, 0>(D, mj);
                     else if (q2 == 0) s += popc_and<CW, 0>(D, mj);
