@@ -635,7 +635,13 @@ def run_chunglu(args):
         ws = cg.alloc_workspace(g.n, g.arcs, mx, device=dev)
     t_order = _events_ms(order_dag)
     per_k = {}
+    prev_ms = None
     for k in range(5, 10):
+        if prev_ms is not None and len(per_k) >= 2:
+            ks_done = sorted(per_k, key=int)
+            growth = per_k[ks_done[-1]]["count_ms"] / max(per_k[ks_done[-2]]["count_ms"], 1e-3)
+            if prev_ms * growth > 60000:  # the next k would take over a minute: stop here
+                break
         pr = torch.zeros(g.n, dtype=torch.int64, device=dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
@@ -648,6 +654,7 @@ def run_chunglu(args):
                              edges_per_s=g.m / ((ms + t_order) * 1e-3),
                              top_root_share=float(p[0] / max(p.sum(), 1)),
                              top100_share=float(p[:100].sum() / max(p.sum(), 1)))
+        prev_ms = ms
         if ms > 60000:
             break
     ks = list(per_k)
