@@ -24,6 +24,7 @@ namespace citron {
 constexpr int kLsWarps = 16;
 constexpr int kMaxListK = CITRON_MAX_K;
 constexpr uint32_t kLsCap = 1024;  // largest out-degree the listing path holds in shared memory
+constexpr uint32_t kStage3Rows = 96;  // k = 3: triangles staged per warp before one flush
 
 struct ListCtx {
     const uint32_t *sL;     // N+(u), DAG ids
@@ -95,6 +96,25 @@ __device__ void walk(const ListCtx &x, uint32_t c, int lane)
     }
 }
 
+// Writes the warp's staged triangles (3 ids each) to the output: one atomic reserves the rows,
+// then the warp copies consecutive words (coalesced).
+__device__ __forceinline__ void flush3(const uint32_t *stage, uint32_t slen, uint32_t *out,
+                                       unsigned long long capacity, unsigned long long *cursor,
+                                       int lane)
+{
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cursor, (unsigned long long)slen);
+    base = __shfl_sync(kFull, base, 0);
+    if (base < capacity) {
+        unsigned long long rows = slen;
+        if (rows > capacity - base) rows = capacity - base;
+        uint32_t *dst = out + base * 3;
+        for (uint32_t g = lane; g < (uint32_t)rows * 3; g += 32) dst[g] = stage[g];
+    }
+    __syncwarp();
+}
+
 template <int K>
 __global__ __launch_bounds__(kLsWarps * 32) void k_list(
     uint32_t n, const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
@@ -117,6 +137,8 @@ __global__ __launch_bounds__(kLsWarps * 32) void k_list(
     x.out = out;
     x.cursor = cursor;
     x.capacity = capacity;
+    uint32_t *stage = rows + (size_t)w * kStage3Rows * 3;  // k = 3 only (no bitmap rows then)
+    uint32_t slen = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_u = atomicAdd(next, 1u);
@@ -139,21 +161,26 @@ __global__ __launch_bounds__(kLsWarps * 32) void k_list(
         }
         const uint32_t W = (D + 31) >> 5, RS = W | 1;
         for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) sL[i] = dag_cols[base + i];
-        for (uint32_t i = threadIdx.x; i < D * RS; i += blockDim.x) rows[i] = 0;
+        if (K > 3)
+            for (uint32_t i = threadIdx.x; i < D * RS; i += blockDim.x) rows[i] = 0;
         __syncthreads();
         const uint32_t lmax = sL[D - 1];
+        const uint32_t mu = out_id(map, u);
         for (uint32_t i = w; i < D; i += nw) {  // row i = N+(u) ∩ N+(a_i)
             const uint32_t a = sL[i];
             if (a >= n) {
                 if (lane == 0) set_error(err, kDevBadInput);
                 continue;
             }
+            const uint32_t ma = K == 3 ? out_id(map, a) : 0u;
             const uint64_t b = dag_off[a], e = dag_off[a + 1];
             for (uint64_t p = b; p < e; p += 32) {
                 const uint32_t y = p + lane < e ? dag_cols[p + lane] : 0xffffffffu;
                 if (__shfl_sync(kFull, y, 0) > lmax) break;
+                bool hit = false;
+                uint32_t lo = 0;
                 if (y <= lmax) {
-                    uint32_t lo = 0, len = D;
+                    uint32_t len = D;
                     while (len > 0) {
                         const uint32_t half = len >> 1;
                         if (sL[lo + half] < y) {
@@ -163,11 +190,29 @@ __global__ __launch_bounds__(kLsWarps * 32) void k_list(
                             len = half;
                         }
                     }
-                    if (lo < D && sL[lo] == y) atomicOr(&rows[i * RS + (lo >> 5)], 1u << (lo & 31));
+                    hit = lo < D && sL[lo] == y;
+                }
+                if constexpr (K == 3) {
+                    // the triangle (u, a_i, y) goes straight to the warp's stage
+                    const uint32_t mask = __ballot_sync(kFull, hit);
+                    if (hit) {
+                        uint32_t *row = stage + 3 * (slen + __popc(mask & lanemask_lt()));
+                        row[0] = mu;
+                        row[1] = ma;
+                        row[2] = out_id(map, y);
+                    }
+                    slen += __popc(mask);
+                    if (slen > kStage3Rows - 32) {
+                        flush3(stage, slen, out, capacity, cursor, lane);
+                        slen = 0;
+                    }
+                } else if (hit) {
+                    atomicOr(&rows[i * RS + (lo >> 5)], 1u << (lo & 31));
                 }
             }
         }
         __syncthreads();
+        if constexpr (K == 3) continue;
         x.RS = RS;
         x.W = W;
         for (;;) {  // edge tasks (u, a_t)
@@ -186,6 +231,8 @@ __global__ __launch_bounds__(kLsWarps * 32) void k_list(
         }
         __syncthreads();
     }
+    if constexpr (K == 3)
+        if (slen) flush3(stage, slen, out, capacity, cursor, lane);
 }
 
 // k = 1: every vertex; k = 2: every arc (row vertex, column).
@@ -233,11 +280,13 @@ size_t list_ws_bytes()
     return s.used;
 }
 
-static size_t list_smem(uint32_t dcap)
+static size_t list_smem(uint32_t dcap, uint32_t k)
 {
     const uint32_t rs_cap = (dcap / 32) | 1;
-    return sizeof(uint32_t) * ((size_t)dcap + (size_t)dcap * rs_cap +
-                               (size_t)kLsWarps * (dcap / 2 + 1 + kMaxListK));
+    size_t rows = (size_t)dcap * rs_cap;
+    const size_t stages = (size_t)kLsWarps * kStage3Rows * 3;
+    if (k == 3 && rows < stages) rows = stages;
+    return sizeof(uint32_t) * ((size_t)dcap + rows + (size_t)kLsWarps * (dcap / 2 + 1 + kMaxListK));
 }
 
 template <int K>
@@ -246,7 +295,7 @@ static cudaError_t launch_list_k(uint32_t n, const uint64_t *dag_off, const uint
                                  unsigned long long capacity, unsigned long long *cursor,
                                  uint32_t *err, cudaStream_t st, int num_sms)
 {
-    const size_t smem = list_smem(dcap);
+    const size_t smem = list_smem(dcap, K);
     cudaError_t e = cudaFuncSetAttribute(k_list<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     int per_sm = 0;
