@@ -61,6 +61,24 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest of every rank's value (the slowest replica sets the job time); x itself on
+    one rank.  Uses the initialised process group (NCCL on GPUs, gloo on the CPU)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of N independent replicas: all ranks' units over the slowest time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def workload():
     from paper_2112_10913_gb300 import graphgen as gg
 
@@ -256,9 +274,7 @@ def run_ours(args, ks):
     if world > 1:
         import torch.distributed as dist
 
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, dev)
         dist.barrier()
 
     # end to end through the host-buffer entry point: H2D of the CSR + order + DAG + count + D2H
@@ -278,16 +294,12 @@ def run_ours(args, ks):
         assert got == ref, "end-to-end counts differ"
     e2e_step = statistics.mean(e2e_ms)
     if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+        e2e_step = max_over_ranks(e2e_step, dev)
 
     if rank != 0:
         return None
     units = m * len(ks) * world
-    value = units / (ms_step / 1e3)
+    value = replica_throughput(m * len(ks), world, ms_step)
     # dominant kernel: the bitmap counting kernel of the largest k
     kd = max(ks, key=lambda k: statistics.mean(r[3][1] for r in per_job[k]))
     kern_ms = statistics.mean(r[3][1] for r in per_job[kd])
