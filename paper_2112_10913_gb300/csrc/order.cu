@@ -61,9 +61,18 @@ __global__ __launch_bounds__(1024) void k_scan_small(uint32_t *data, uint32_t co
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t seg = ((count + 31) / 32 + 31) & ~31u;
     const uint32_t lo = min(count, (uint32_t)w * seg), hi = min(count, lo + seg);
+    constexpr int kBatch = 8;  // loads of one lane in flight together
     uint32_t sum = 0;
-#pragma unroll 4
-    for (uint32_t i = lo + lane; i < hi; i += 32) sum += data[i];
+    for (uint32_t b = lo; b < hi; b += 32 * kBatch) {
+        uint32_t v[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; t++) {
+            const uint32_t i = b + t * 32 + lane;
+            v[t] = i < hi ? data[i] : 0u;
+        }
+#pragma unroll
+        for (int t = 0; t < kBatch; t++) sum += v[t];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
     if (lane == 0) s_warp[w] = sum;
@@ -75,12 +84,20 @@ __global__ __launch_bounds__(1024) void k_scan_small(uint32_t *data, uint32_t co
     }
     __syncthreads();
     uint32_t carry = s_warp[w];
-    for (uint32_t i0 = lo; i0 < hi; i0 += 32) {
-        const uint32_t i = i0 + lane;
-        const uint32_t v = i < hi ? data[i] : 0u;
-        const uint32_t incl = warp_incl_scan(v);
-        if (i < hi) data[i] = carry + incl - v;
-        carry += __shfl_sync(kFull, incl, 31);
+    for (uint32_t b = lo; b < hi; b += 32 * kBatch) {
+        uint32_t v[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; t++) {
+            const uint32_t i = b + t * 32 + lane;
+            v[t] = i < hi ? data[i] : 0u;
+        }
+#pragma unroll
+        for (int t = 0; t < kBatch; t++) {
+            const uint32_t i = b + t * 32 + lane;
+            const uint32_t incl = warp_incl_scan(v[t]);
+            if (i < hi) data[i] = carry + incl - v[t];
+            carry += __shfl_sync(kFull, incl, 31);
+        }
     }
 }
 

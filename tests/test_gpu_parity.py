@@ -28,6 +28,10 @@ SMALL_GRAPHS = {
     "rmat-n6000": lambda: gg.small_rmat(21, 6000, 24.0),
     "er-n9000": lambda: gg.small_er(22, 9000, 18.0),
     "rmat-n50000": lambda: gg.small_rmat(23, 50000, 30.0),
+    # degree ~2 and ~1.5: a tile of arcs spans thousands of rows (and many rows are empty)
+    "path-n30000": lambda: gg.csr_from_edges(30000, np.arange(29999, dtype=np.uint32),
+                                             np.arange(1, 30000, dtype=np.uint32)),
+    "er-n20000-sparse": lambda: gg.small_er(24, 20000, 1.5),
 }
 
 
