@@ -119,3 +119,25 @@ def test_chunglu_sampled_roots(oracle_lib, chunglu, dev3, k):
     assert pick.size > 1000
     _, want = oracle_lib.count_roots(off, cols, n, k, pick.astype(np.uint32), per_root=True)
     assert np.array_equal(got[pick], want)
+
+
+# ---- the 4,096-graph batch at full size -----------------------------------------------------
+
+def test_full_batch_sampled_graphs(gpu, oracle_lib):
+    """The whole 4,096-graph batch (n log-uniform in [50, 50000], ER/R-MAT, k in 3..7), counted in
+    one batched launch sequence; a seeded sample of 40 graphs that the oracle finishes quickly
+    (count <= 1e8, n <= 20000) must match the oracle, and every batched count must match the
+    graph's own launch sequence on a second seeded sample."""
+    from paper_2112_10913_gb300.batch import BatchCounter
+
+    items = gg.config4_batch_parallel(seed=4, count=4096)
+    bc = BatchCounter([it.graph for it in items], [it.k for it in items])
+    bc.launch()
+    got = bc.result()
+    order = gg.permutation(4, 9, len(items))
+    picked = [int(i) for i in order if got[int(i)] <= 1e8 and items[int(i)].graph.n <= 20000][:40]
+    assert len(picked) == 40
+    for i in picked:
+        assert got[i] == oracle_lib.count_graph(items[i].graph, items[i].k), i
+    for i in [int(i) for i in order[-64:]]:
+        assert got[i] == gpu.DeviceGraph(items[i].graph).count(items[i].k), i

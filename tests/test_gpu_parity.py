@@ -156,6 +156,13 @@ def test_triangles_trace_config1(gpu):
 
 
 def test_edge_cases(gpu, oracle_lib):
+    # the empty graph: every entry point accepts n = 0
+    g = gg.csr_from_edges(0, [], [])
+    for relabel in (True, False):
+        G = gpu.DeviceGraph(g, relabel=relabel)
+        assert [G.count(k) for k in (1, 2, 3, 5)] == [0, 0, 0, 0]
+    assert gpu.DeviceGraph(g, ordering="core").count(3) == 0
+    assert gpu.DeviceGraph(g).list(3).shape[0] == 0
     # isolated vertices only
     g = gg.csr_from_edges(10, [], [])
     G = gpu.DeviceGraph(g)
