@@ -344,7 +344,8 @@ class DeviceGraph:
         id_map = None
         if input_ids and self.rank is not None:
             id_map = torch.empty_like(self.rank)
-            id_map[self.rank.long()] = torch.arange(self.n, dtype=torch.int32, device=self.rank.device)
+            id_map[self.rank[: self.n].long()] = torch.arange(self.n, dtype=torch.int32,
+                                                              device=self.rank.device)
         got = citron_list(self.n, self.dag_off, self.dag_cols, k, self.ws, out, total, id_map, stream)
         if got != total:
             raise RuntimeError("clique count changed between the sizing and the listing call")
