@@ -501,6 +501,8 @@ __global__ __launch_bounds__(kRlWarps * 32) void k_rl_sort(
     __shared__ uint64_t s_g[kRlRows + 1];
     __shared__ uint64_t s_dst[kRlRows];
     __shared__ uint32_t s_vals[kRlStage];
+    __shared__ uint8_t s_rowid[kRlStage];  // row (within the step) of each staged entry of a short row
+    static_assert(kRlRows <= 256, "row ids are 8-bit");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (uint32_t r0 = blockIdx.x * kRlRows; r0 < n; r0 += gridDim.x * kRlRows) {
         const uint32_t cnt = min(kRlRows, n - r0);
@@ -514,20 +516,22 @@ __global__ __launch_bounds__(kRlWarps * 32) void k_rl_sort(
         const uint64_t base = s_g[0];
         const uint64_t total = s_g[cnt] - base;
         const bool staged = total <= kRlStage;
-        if (staged)
+        if (staged) {
             for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) s_vals[i] = vals[base + i];
+            for (uint32_t i = w; i < cnt; i += kRlWarps) {  // row ids of the short rows' entries
+                const uint32_t rb = (uint32_t)(s_g[i] - base), re = (uint32_t)(s_g[i + 1] - base);
+                if (re - rb <= 32 && rb + lane < re) s_rowid[rb + lane] = (uint8_t)i;
+            }
+        }
         __syncthreads();
         // short rows: one thread per staged entry
         if (staged) {
             for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                uint32_t lo = 0, hi = cnt - 1;  // row of entry e: last i with s_g[i] - base <= e
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) >> 1;
-                    if (s_g[mid] - base <= e) lo = mid;
-                    else hi = mid - 1;
-                }
+                // entries of long rows hold a stale id: the range check sends them to the warps
+                const uint32_t lo = s_rowid[e];
+                if (lo >= cnt) continue;
                 const uint32_t rb = (uint32_t)(s_g[lo] - base), len = (uint32_t)(s_g[lo + 1] - s_g[lo]);
-                if (len > 32) continue;
+                if (e < rb || e >= rb + len || len > 32) continue;
                 const uint64_t dst = s_dst[lo];
                 if (dst == ~0ull || dst + len > dag_cap) {
                     set_error(err, kDevBadInput);
