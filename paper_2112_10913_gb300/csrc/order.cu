@@ -408,22 +408,6 @@ __device__ __forceinline__ void bitonic_smem(uint32_t *s, uint32_t p, int lane, 
     }
 }
 
-// Ascending bitonic sort of one value per lane (32 values) with shuffles.
-__device__ __forceinline__ uint32_t bitonic_warp(uint32_t x, int lane)
-{
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const uint32_t y = __shfl_xor_sync(kFull, x, j);
-            const bool up = (lane & k) == 0;
-            const bool lower = (lane & j) == 0;
-            x = (lower == up) ? min(x, y) : max(x, y);
-        }
-    }
-    return x;
-}
-
 // Ascending bitonic sort of 32*E values held by one warp in registers, striped: value e of
 // lane l has index e*32 + l.  Partners closer than 32 are on other lanes (shuffles), farther
 // ones are in the same lane's registers.
