@@ -222,8 +222,9 @@ __device__ __forceinline__ uint32_t tri_rounds(const WarpCtx &x, const uint32_t 
 // its induced sub-DAG: row i = the members j that are out-neighbours of member i, packed into
 // CW = ceil(s/32) <= 4 words ("compact rows"; upper-triangular when the DAG is relabelled to its
 // order).  The remaining levels of the recursion then work on at most 4 words per set instead
-// of the root-wide span; a row is one 16-byte shared-memory load.  (Wider sets stay on the
-// root-wide bitmap: 8-word compact rows were measured slower on R-MAT 20.)
+// of the root-wide span; a row is one 16-byte shared-memory load.  At R = 3, sets of 129..192
+// members take packed rows of 5 or 6 words (below); wider sets stay on the root-wide bitmap
+// (full 8-word rows for every level were measured slower on R-MAT 20).
 //
 // Bits are gathered word by word with the parallel-suffix "compress" of H. S. Warren, Hacker's
 // Delight (2nd ed., Sec. 7-4): for a mask m the five move masks depend on m only, so they are
@@ -257,7 +258,8 @@ __device__ __forceinline__ uint32_t compress_with(uint32_t x, uint32_t m, const 
 }
 
 // Builds the compact rows of the s members of the candidate set (words in cbuf, members in
-// elem, non-zero words [clo, chi)).  NW = 4 or 8 output words per row.
+// elem, non-zero words [clo, chi)).  NW = 4 output words per row (one uint4) is the width in
+// use; NW = 8 (two uint4) is kept for wider experiments.
 template <int NW>
 __device__ __forceinline__ void build_compact(const WarpCtx &x, uint32_t s, int clo, int chi, int lane)
 {
@@ -639,6 +641,8 @@ __device__ __forceinline__ void compact_entry(const WarpCtx &x, uint32_t c, int 
 
 // Counts the R-cliques inside the candidate set whose word w sits in lane w (words >= W are
 // zero); adds lane-partial sums to acc.
+//   R >= 3, triangular layout, at most compact_max (R >= 4) or compact3_max (R == 3) members:
+//           re-encoded compactly (compact_entry) and finished on the compact rows.
 //   R >= 4: warp-uniform walk over the members a; the next candidate set c ∧ row_a is again
 //           spread over the lanes (one shared-memory load per lane).
 //   R == 3: members are compacted and dealt to lanes; each lane builds its own c ∧ row_a and
