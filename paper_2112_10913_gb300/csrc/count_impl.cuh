@@ -259,7 +259,7 @@ __device__ __forceinline__ uint32_t compress_with(uint32_t x, uint32_t m, const 
 
 // Builds the compact rows of the s members of the candidate set (words in cbuf, members in
 // elem, non-zero words [clo, chi)).  NW = 4 output words per row (one uint4) is the width in
-// use; NW = 8 (two uint4) is kept for wider experiments.
+// use; NW = 8 (two uint4 per row) is also supported.
 template <int NW>
 __device__ __forceinline__ void build_compact(const WarpCtx &x, uint32_t s, int clo, int chi, int lane)
 {
