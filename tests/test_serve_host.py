@@ -1,0 +1,103 @@
+"""Host logic of the serving engine, on the CPU: lanes, FIFO micro-batches bounded by request
+count and arcs, admission by the HBM-footprint budget, and every request answered once.  The
+CUDA pieces (streams, device selection) are replaced by stand-ins and each micro-batch is
+counted by the oracle, so no GPU is needed."""
+import contextlib
+import threading
+import time
+
+import pytest
+import torch
+
+import oracle
+from paper_2112_10913_gb300 import graphgen as gg
+
+
+class _FakeStream:
+    def __init__(self, device=None, priority=0):
+        self.priority = priority
+
+
+class _Props:
+    multi_processor_count = 152
+
+
+@pytest.fixture
+def engine_cls(monkeypatch):
+    monkeypatch.setattr(torch.cuda, "Stream", _FakeStream)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: _Props())
+    from paper_2112_10913_gb300 import serve
+
+    class Recording(serve.ServeEngine):
+        def __init__(self, *a, **kw):
+            self.seen = []
+            self.max_bytes = 0
+            self.rec_lock = threading.Lock()
+            super().__init__(*a, **kw)
+
+        def _run_batch(self, batch, stream, max_blocks=0):
+            with self.rec_lock:
+                self.seen.append(([r.rid for r in batch], stream.priority, max_blocks))
+                self.max_bytes = max(self.max_bytes, self.in_flight_bytes)
+            time.sleep(0.002)
+            return [oracle.count_graph(r.graph, r.k, threads=1) for r in batch]
+
+    return serve, Recording
+
+
+def test_lanes_batches_and_answers(engine_cls):
+    serve, Recording = engine_cls
+    light = [gg.small_er(i, 300, 6.0) for i in range(30)]
+    heavy = gg.small_rmat(99, 3000, 30.0)
+    reqs = [serve.Request(i, g, 3 + i % 3, arrival=0.0005 * i) for i, g in enumerate(light)]
+    reqs += [serve.Request(100 + j, heavy, 4, arrival=0.004 * j) for j in range(3)]
+    cfg = serve.ServeConfig(slots=2, max_batch_requests=4, heavy_arcs=heavy.arcs, heavy_slots=1,
+                            heavy_sm_fraction=0.5)
+    eng = Recording(cfg, device="cuda:0")
+    try:
+        done = eng.run(reqs, timeout_s=60)
+    finally:
+        eng.close()
+    assert eng.heavy_max_blocks == 76
+    assert sorted(r.rid for r in done) == sorted(r.rid for r in reqs)
+    for r in done:
+        assert r.count == oracle.count_graph(r.graph, r.k, threads=1)
+        assert r.done >= r.admitted >= r.arrival - 1e-9
+    by_rid = {r.rid: r for r in done}
+    for rids, prio, mb in eng.seen:
+        assert 1 <= len(rids) <= 4
+        kinds = {by_rid[i].heavy for i in rids}
+        assert len(kinds) == 1  # a micro-batch never mixes the lanes
+        if kinds == {True}:
+            assert prio == 0 and mb == 76
+        else:
+            assert prio == -1 and mb == 0
+    # FIFO within each lane: micro-batches are numbered as they are admitted, and a later
+    # arrival never lands in an earlier micro-batch (slots may still finish out of order)
+    for heavy_lane in (False, True):
+        lane_reqs = sorted((r for r in done if r.heavy == heavy_lane), key=lambda r: r.arrival)
+        ids = [r.batch for r in lane_reqs]
+        assert ids == sorted(ids)
+    s = serve.summarize(done)
+    assert s["requests"] == len(reqs) and "light" in s and "heavy" in s
+
+
+def test_admission_keeps_the_footprint_under_budget(engine_cls):
+    serve, Recording = engine_cls
+    graphs = [gg.small_er(i, 400, 8.0) for i in range(8)]
+    arcs = max(g.arcs for g in graphs)
+    one = serve.footprint_bytes(400, arcs)
+    extra = serve.footprint_bytes(800, 2 * arcs) - one
+    budget = one + extra // 2  # room for one request in flight, never two
+    cfg = serve.ServeConfig(slots=3, max_batch_requests=8, hbm_budget_bytes=budget, heavy_arcs=0)
+    eng = Recording(cfg, device="cuda:0")
+    try:
+        done = eng.run([serve.Request(i, g, 3, arrival=0.0) for i, g in enumerate(graphs)],
+                       timeout_s=60)
+    finally:
+        eng.close()
+    assert eng.max_bytes <= budget
+    assert len({r.batch for r in done}) == len(graphs)  # admitted one by one
+    assert eng.heavy_slots == []
