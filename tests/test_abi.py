@@ -83,3 +83,37 @@ def test_workspace_size_grows_with_graph(built):
     assert 0 < a < b
     # above the bitmap limit the sorted-list scratch is added
     assert cg.citron_workspace_bytes(1000, 20000, 5000) > a
+
+
+def test_plain_c_caller_links_and_runs(built, tmp_path):
+    """A plain C program (no C++, no torch) includes the header, links libcitron.so and gets
+    answers that need no GPU: the version, status strings, workspace sizes, argument checks."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "caller.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "citron.h"
+int main(void) {
+    uint64_t count = 0;
+    if (citron_version() < 100) return 1;
+    if (strcmp(citron_status_str(CITRON_OK), "ok") != 0) return 2;
+    if (citron_workspace_bytes(1000, 20000, 100) == 0) return 3;
+    /* k = 0 is invalid before any device work */
+    if (citron_count(10, (const uint64_t *)1, (const uint32_t *)1, 0, 0, &count, NULL, NULL, 0, NULL)
+        != CITRON_E_INVALID) return 4;
+    printf("ok %d\n", citron_version());
+    return 0;
+}
+""")
+    exe = tmp_path / "caller"
+    lib_dir = Path(built).parent
+    subprocess.run(["gcc", "-std=c99", "-Wall", f"-I{ROOT / 'include'}", str(src), "-o", str(exe),
+                    f"-L{lib_dir}", "-lcitron", f"-Wl,-rpath,{lib_dir}"], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("ok ")
