@@ -71,3 +71,25 @@ def test_parallel_batch_equals_serial():
     b = gg.config4_batch_parallel(seed=9, count=6, n_range=(50, 300), workers=2)
     for x, y in zip(a, b):
         assert x.k == y.k and np.array_equal(x.graph.off, y.graph.off) and np.array_equal(x.graph.cols, y.graph.cols)
+
+
+def test_union_csr_for_batching():
+    """The batch's union CSR: every graph's rows shifted by the vertices before it, the group map
+    names each vertex's graph, the CSR contract holds, and (disjoint-union additivity) the
+    oracle's count of the union is the sum of the graphs' counts for every k."""
+    import oracle
+    from paper_2112_10913_gb300.batch import union_csr
+
+    graphs = [gg.fig1(), gg.csr_from_edges(3, [], []), gg.complete(6), gg.small_er(5, 200, 8.0)]
+    u, group = union_csr(graphs)
+    assert u.n == sum(g.n for g in graphs) and u.arcs == sum(g.arcs for g in graphs)
+    assert oracle.validate(u.off, u.cols, u.n) == 0
+    base = 0
+    for i, g in enumerate(graphs):
+        assert np.all(group[base: base + g.n] == i)
+        for v in range(g.n):
+            row = u.cols[u.off[base + v]: u.off[base + v + 1]]
+            assert np.array_equal(row, g.cols[g.off[v]: g.off[v + 1]] + base)
+        base += g.n
+    for k in (1, 2, 3, 4, 5):
+        assert oracle.count_graph(u, k) == sum(oracle.count_graph(g, k) for g in graphs)
