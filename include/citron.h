@@ -233,8 +233,7 @@ citron_status citron_workspace_status(void *ws, void *stream);
 /*
  * citron_count_noalloc -- citron_count for callers that cannot allocate device memory.  (The
  * paper has no counterpart: this is an interface choice of this library.)
- *   Who needs it: code running while a stream is captured into a CUDA graph (allocation is not
- *   allowed there), host applications or plugin frameworks that own the device heap and forbid
+ *   Who needs it: host applications or plugin frameworks that own the device heap and forbid
  *   allocation after start-up, real-time loops that cannot take the implicit synchronisation of
  *   cudaMalloc/cudaFree, and C callers with no allocator of their own.  They still pass the DAG
  *   (input) and receive the count (output); no workspace is needed.

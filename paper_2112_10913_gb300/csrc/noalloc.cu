@@ -1,11 +1,10 @@
 // noalloc.cu -- k-clique counting for callers that cannot allocate device memory.
 //
 // citron_count needs a caller-provided workspace.  Some callers have no way to provide one:
-// code that runs while a CUDA stream is being captured into a graph (allocation calls are not
-// allowed there), host applications and plugin frameworks that own the device heap and forbid
-// allocation after start-up, real-time loops that cannot afford the implicit synchronisation of
-// cudaMalloc/cudaFree, and plain C callers that have no allocator of their own.  For them this
-// file keeps the counting scratch in one fixed, file-scope device array.
+// host applications and plugin frameworks that own the device heap and forbid allocation after
+// start-up, real-time loops that cannot afford the implicit synchronisation of cudaMalloc and
+// cudaFree, and plain C callers that have no allocator of their own.  For them this file keeps
+// the counting scratch in one fixed, file-scope device array.
 //
 // The array is a static __device__ object: every GPU that loads the library holds its
 // kNoAllocBytes until the process exits.  In host code the symbol is only a host-side stand-in,

@@ -104,9 +104,11 @@ class _Slot:
                 now = self.engine.now()
                 for r in batch:
                     r.done = now
-            self.engine._release(self, batch)
+            # the slot must be idle before it goes back on the free list: once released, the
+            # dispatcher may hand it the next micro-batch at any moment
             with self.cv:
                 self.work = None
+            self.engine._release(self, batch)
 
     def give(self, batch: list[Request]):
         with self.cv:

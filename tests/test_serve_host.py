@@ -101,3 +101,30 @@ def test_admission_keeps_the_footprint_under_budget(engine_cls):
     assert eng.max_bytes <= budget
     assert len({r.batch for r in done}) == len(graphs)  # admitted one by one
     assert eng.heavy_slots == []
+
+
+def test_slot_handoff_never_loses_a_request(engine_cls):
+    """A slot returns to the free list only once it is idle: with one slot and many one-request
+    micro-batches handed over back to back, every request is answered.  The release is slowed
+    down so that the dispatcher hands over the next micro-batch while the slot's thread is still
+    inside it: a slot that clears its work after the release loses that micro-batch."""
+    serve, _ = engine_cls
+
+    class Instant(serve.ServeEngine):
+        def _run_batch(self, batch, stream, max_blocks=0):
+            return [r.k for r in batch]
+
+        def _release(self, slot, batch):
+            super()._release(slot, batch)
+            time.sleep(0.001)
+
+    g = gg.fig1()
+    reqs = [serve.Request(i, g, 3, arrival=0.0) for i in range(2000)]
+    eng = Instant(serve.ServeConfig(slots=1, max_batch_requests=1, heavy_arcs=0, poll_s=0.0),
+                  device="cuda:0")
+    try:
+        done = eng.run(reqs, timeout_s=60)
+    finally:
+        eng.close()
+    assert len(done) == len(reqs) and all(r.count == 3 for r in done)
+    assert len({r.batch for r in done}) == len(reqs)
