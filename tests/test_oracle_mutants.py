@@ -29,6 +29,9 @@ MUTANTS = [
     ("rounds-level-falls", "if (least > level) level = least;", "level = least;"),
     ("rounds-stale-members", "                now[u] = 0;\n", ""),
     ("list-depth", "int depth = L->k - r; /* vertices already chosen */", "int depth = L->k - r - (r > 2);"),
+    ("per-root-slot", "if (p->per_root) p->per_root[t] = c;", "if (p->per_root) p->per_root[u % p->nroots] = c;"),
+    ("per-edge-slot", "st = cnt(&g, levels[0], len, k - 2, levels + 1, &per_edge[e]);",
+     "st = cnt(&g, levels[0], len, k - 2, levels + 1, &per_edge[dag_off[u] + dag_off[u + 1] - 1 - e]);"),
     ("prefix-sum", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u];", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u] - (count[u] > 2);"),
 ]
 
@@ -84,6 +87,28 @@ def pins_hold() -> bool:
             if len(rows) != want or len({frozenset(r) for r in rows}) != want:
                 return False
             if any(b not in adj[a] for r in rows for a, b in itertools.combinations(r, 2)):
+                return False
+        # per-root values for a shuffled subset of roots, and per-edge values, against brute
+        # force: cliques whose first (first two) vertices in the degree order they are
+        g = gg.random_small(7, 13, 0.6)
+        off, cols = oracle.gen_ordering(g.off, g.cols, g.n)
+        adj = [set(g.cols[g.off[v]: g.off[v + 1]].tolist()) for v in range(g.n)]
+        deg = np.diff(g.off)
+        roots = np.array([5, 11, 0, 7, 2, 9, 12, 3], dtype=np.uint32)
+        for k in (3, 4):
+            want_root, want_edge = [0] * g.n, {}
+            for s in itertools.combinations(range(g.n), k):
+                if all(b in adj[a] for a, b in itertools.combinations(s, 2)):
+                    o = sorted(s, key=lambda v: (int(deg[v]), v))
+                    want_root[o[0]] += 1
+                    want_edge[(o[0], o[1])] = want_edge.get((o[0], o[1]), 0) + 1
+            _, pr = oracle.count_roots(off, cols, g.n, k, roots, threads=1, per_root=True)
+            if [int(x) for x in pr] != [want_root[r] for r in roots]:
+                return False
+            pe = oracle.count_per_edge(off, cols, g.n, k)
+            got_edge = {(u, int(cols[e])): int(pe[e]) for u in range(g.n)
+                        for e in range(int(off[u]), int(off[u + 1])) if pe[e]}
+            if got_edge != want_edge:
                 return False
         return True
     except Exception:

@@ -253,6 +253,58 @@ def test_per_root_and_per_edge_sum_to_total(oracle_lib):
         assert int(pe.sum()) == tot == s == int(pr.sum())
 
 
+def brute_first_two(g, k, key):
+    """For every k-clique (brute force over k-subsets), its first and second vertex when the
+    vertices are ordered by key (smaller first): the root that counts it (Sec. II, every clique is
+    counted once at its first vertex in the DAG order) and the edge task (root, second) that
+    reaches it in the edge-parallel form."""
+    adj = adjacency_sets(g)
+    out = []
+    for s in itertools.combinations(range(g.n), k):
+        if all(b in adj[a] for a, b in itertools.combinations(s, 2)):
+            o = sorted(s, key=key)
+            out.append((o[0], o[1] if k > 1 else None))
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+@pytest.mark.parametrize("relabel", [False, True])
+def test_per_root_and_per_edge_values_equal_brute_force(oracle_lib, seed, relabel):
+    """Every per-root value (for a shuffled subset of roots) and every per-edge value equals the
+    number of brute-force k-cliques whose first vertex (first two vertices) in the DAG order it is.
+    Two DAG layouts: Algorithm GenOrdering's (input ids, degree order) and a DAG relabelled to a
+    seeded random order (row r = the vertex of rank r)."""
+    rng = np.random.default_rng(100 + seed)
+    n = 14 + seed
+    g = gg.random_small(seed + 40, n, 0.55)
+    deg = np.diff(g.off).astype(np.int64)
+    if relabel:
+        rank = rng.permutation(n).astype(np.uint32)
+        off, cols = oracle_lib.dag_by_rank(g.off, g.cols, n, rank, relabel=True)
+        key = lambda u: int(rank[u])
+        name = lambda u: int(rank[u])  # DAG id of input vertex u
+    else:
+        off, cols = oracle_lib.gen_ordering(g.off, g.cols, n)
+        key = lambda u: (int(deg[u]), u)
+        name = lambda u: u
+    roots = rng.permutation(n)[: n - 3].astype(np.uint32)  # shuffled, not all vertices
+    for k in (3, 4, 5):
+        firsts = brute_first_two(g, k, key)
+        want_root = np.zeros(n, dtype=np.int64)
+        want_edge = {}
+        for a, b in firsts:
+            want_root[name(a)] += 1
+            want_edge[(name(a), name(b))] = want_edge.get((name(a), name(b)), 0) + 1
+        tot, pr = oracle_lib.count_roots(off, cols, n, k, roots, per_root=True)
+        assert [int(x) for x in pr] == [int(want_root[r]) for r in roots]
+        assert tot == int(want_root[roots].sum())
+        pe = oracle_lib.count_per_edge(off, cols, n, k)
+        for u in range(n):
+            for e in range(int(off[u]), int(off[u + 1])):
+                assert int(pe[e]) == want_edge.pop((u, int(cols[e])), 0), (k, u, int(cols[e]))
+        assert not want_edge  # every (root, second) pair is an arc of the DAG
+
+
 def degeneracy_brute(g):
     adj = adjacency_sets(g)
     best = 0
