@@ -231,6 +231,35 @@ citron_status citron_count_batch(uint32_t n, const uint64_t *d_dag_off, const ui
 citron_status citron_workspace_status(void *ws, void *stream);
 
 /*
+ * citron_set_faults -- fault injection for tests of the error paths (the paper has no
+ * counterpart: the method itself never fails).  Process-wide; applies to every call made after it
+ * on any device until it is called again; NULL restores normal operation.  Nothing here faults
+ * a GPU: every injected failure is a wait that nothing will end, which the library's own bounded
+ * waits must turn into CITRON_E_TIMEOUT, or a seeded sum that must report CITRON_E_OVERFLOW.
+ *   lookback_spin_limit : probes a decoupled look-back makes before it gives up (0: 2^22);
+ *   lookback_stall_tile : tile index + 1 whose look-back never publishes its prefix, so that
+ *                         the next tile's wait must run out (0: none);
+ *   barrier_wait_ns     : time a grid barrier of the core ordering waits (0: 4 s);
+ *   barrier_absent_block: block index + 1 of the core ordering that never arrives at the first
+ *                         grid barrier, so that the others' wait must run out (0: none);
+ *   count_seed          : initial value of the device totals of counting passes (citron_count
+ *                         and its variants: the grand total; citron_count_batch: every graph's
+ *                         total); a count that carries it past 2^64 - 1 reports
+ *                         CITRON_E_OVERFLOW (0: none).
+ * Results computed while a fault is injected are not valid; calls still return a status.
+ */
+typedef struct {
+    uint32_t lookback_spin_limit;
+    uint32_t lookback_stall_tile;
+    uint64_t barrier_wait_ns;
+    uint32_t barrier_absent_block;
+    uint32_t reserved;
+    uint64_t count_seed;
+} citron_faults;
+
+citron_status citron_set_faults(const citron_faults *faults);
+
+/*
  * citron_count_noalloc -- citron_count for callers that cannot allocate device memory.  (The
  * paper has no counterpart: this is an interface choice of this library.)
  *   Who needs it: host applications or plugin frameworks that own the device heap and forbid

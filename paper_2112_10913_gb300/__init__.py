@@ -44,6 +44,7 @@ EXPORTS = (
     "citron_count_noalloc",
     "citron_count_batch",
     "citron_workspace_status",
+    "citron_set_faults",
 )
 
 COUNT_TIME_KERNELS = 1
@@ -63,6 +64,19 @@ class CountOpts(ctypes.Structure):
         ("d_per_root", ctypes.c_void_p),
         ("work_ops", ctypes.c_uint64),
         ("kernel_ms", ctypes.c_float * 3),
+    ]
+
+
+class Faults(ctypes.Structure):
+    """Mirror of citron_faults (include/citron.h): fault injection for error-path tests."""
+
+    _fields_ = [
+        ("lookback_spin_limit", ctypes.c_uint32),
+        ("lookback_stall_tile", ctypes.c_uint32),
+        ("barrier_wait_ns", ctypes.c_uint64),
+        ("barrier_absent_block", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("count_seed", ctypes.c_uint64),
     ]
 
 
@@ -118,6 +132,8 @@ def lib() -> ctypes.CDLL:
     L.citron_count_batch.restype = i32
     L.citron_workspace_status.argtypes = [vp, vp]
     L.citron_workspace_status.restype = i32
+    L.citron_set_faults.argtypes = [vp]
+    L.citron_set_faults.restype = i32
     _lib = L
     return L
 
@@ -239,6 +255,19 @@ def citron_count_batch(n: int, dag_off, dag_cols, rank, group_of_vertex, group_k
                                     max_outdeg, ctypes.byref(opts) if opts is not None else None,
                                     _dptr(counts), _dptr(ws), _nbytes(ws), _stream(stream)),
            "citron_count_batch")
+
+
+def citron_set_faults(lookback_spin_limit: int = 0, lookback_stall_tile: int | None = None,
+                      barrier_wait_ns: int = 0, barrier_absent_block: int | None = None,
+                      count_seed: int = 0):
+    """Inject faults for error-path tests (tile / block indices are 0-based here; None: none).
+    Call with no arguments to restore normal operation."""
+    f = Faults(lookback_spin_limit, 0 if lookback_stall_tile is None else lookback_stall_tile + 1,
+               barrier_wait_ns, 0 if barrier_absent_block is None else barrier_absent_block + 1, 0,
+               count_seed)
+    clear = not any((lookback_spin_limit, lookback_stall_tile is not None, barrier_wait_ns,
+                     barrier_absent_block is not None, count_seed))
+    _check(lib().citron_set_faults(None if clear else ctypes.byref(f)), "citron_set_faults")
 
 
 def citron_workspace_status(ws, stream=None):

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "citron.h"
 #include "common.cuh"
@@ -37,6 +38,15 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
 static std::atomic<unsigned long long> g_launches{0};
 void note_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
+static std::mutex g_fault_mutex;
+static citron_faults g_faults = {};
+citron_faults injected_faults()
+{
+    std::lock_guard<std::mutex> lock(g_fault_mutex);
+    return g_faults;
+}
+cudaError_t seed_totals(unsigned long long *p, uint32_t count, cudaStream_t s);
 cudaError_t launch_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
                                     unsigned long long *per_root, cudaStream_t s);
 cudaError_t run_count_async(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
@@ -335,6 +345,7 @@ citron_status citron_count_batch(uint32_t n, const uint64_t *d_dag_off, const ui
     if (!c.ok) return CITRON_E_WORKSPACE;
     unsigned long long *counts = (unsigned long long *)d_counts;
     cudaError_t e = ngroups ? cudaMemsetAsync(counts, 0, (size_t)ngroups * 8, s) : cudaSuccess;
+    if (!e) e = seed_totals(counts, ngroups, s);
     const uint32_t *gor = d_group_of_vertex;
     if (!e && d_rank) {
         e = launch_batch_rows(n, d_rank, d_group_of_vertex, group_of_row, err_word(ws), s);
@@ -358,6 +369,13 @@ citron_status citron_count_batch(uint32_t n, const uint64_t *d_dag_off, const ui
                             sm_count());
     }
     return from_cuda(e);
+}
+
+citron_status citron_set_faults(const citron_faults *faults)
+{
+    std::lock_guard<std::mutex> lock(g_fault_mutex);
+    g_faults = faults ? *faults : citron_faults{};
+    return CITRON_OK;
 }
 
 citron_status citron_workspace_status(void *ws, void *stream)

@@ -33,6 +33,14 @@ __device__ __forceinline__ void set_error(uint32_t *err, uint32_t code)
 // (~1 us under load), so the limit bounds a wait to a few seconds at most.
 constexpr uint32_t kSpinLimit = 1u << 22;
 
+// Bounds of the decoupled look-back waits, passed to every kernel that waits on another tile:
+// the spin limit and, for fault-injection tests only, a tile that never publishes its prefix
+// (~0u: none), so that its successor's bounded wait must run out.
+struct WaitCfg {
+    uint32_t spin_limit = kSpinLimit;
+    uint32_t stall_tile = 0xffffffffu;
+};
+
 // Exact uint64 accumulation into a global counter; flags a wrap past 2^64 - 1.
 __device__ __forceinline__ void add_checked(unsigned long long *dst, unsigned long long v,
                                             uint32_t *err)
@@ -123,9 +131,11 @@ __device__ __forceinline__ unsigned long long peek(unsigned long long *status, l
 // Called by ONE full warp of the tile's block.  Returns the exclusive prefix of tile t and
 // publishes its inclusive prefix.  `agg` must be the same on all lanes.
 __device__ __forceinline__ unsigned long long lookback_warp(unsigned long long *status, uint32_t t,
-                                                            unsigned long long agg, uint32_t *err)
+                                                            unsigned long long agg, uint32_t *err,
+                                                            const WaitCfg &wc)
 {
     const int lane = threadIdx.x & 31;
+    if (t == wc.stall_tile) return 0;  // injected fault: this tile never publishes
     if (t == 0) {
         if (lane == 0) publish(status, 0, kFlagPre | agg);
         return 0;
@@ -142,7 +152,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(unsigned long long *
         uint32_t zero = __ballot_sync(kFull, flag == 0);
         uint32_t upto = pre ? ((__ffs(pre) == 32) ? kFull : ((1u << __ffs(pre)) - 1)) : kFull;
         if (zero & upto) {
-            if (++spins > kSpinLimit) {
+            if (++spins > wc.spin_limit) {
                 if (lane == 0) set_error(err, kDevTimeout);
                 break;
             }
@@ -225,6 +235,18 @@ struct CountRun {
 // Number of kernels this library has launched (all devices, all threads).
 void note_launches(unsigned n);
 unsigned long long launches();
+
+// Faults injected by citron_set_faults (all zero in normal operation).
+citron_faults injected_faults();
+// Look-back bounds under the injected faults.
+inline citron::WaitCfg wait_cfg()
+{
+    const citron_faults f = injected_faults();
+    citron::WaitCfg w;
+    if (f.lookback_spin_limit) w.spin_limit = f.lookback_spin_limit;
+    if (f.lookback_stall_tile) w.stall_tile = f.lookback_stall_tile - 1;
+    return w;
+}
 
 struct Carver {
     char *base;

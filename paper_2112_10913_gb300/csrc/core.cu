@@ -50,9 +50,9 @@ __device__ __forceinline__ uint32_t load_relaxed(unsigned int *p)
 }
 
 // Barrier over all blocks of a cooperative launch (all of them resident).  Returns false on every
-// thread of the block when the wait gave up or some block has reported an error, so that the
-// kernel can return; the other blocks then give up at their next barrier.
-__device__ bool grid_barrier(CoreState *s, uint32_t *err)
+// thread of the block when the wait (at most wait_ns) gave up or some block has reported an
+// error, so that the kernel can return; the other blocks then give up at their next barrier.
+__device__ bool grid_barrier(CoreState *s, uint32_t *err, unsigned long long wait_ns)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -68,7 +68,7 @@ __device__ bool grid_barrier(CoreState *s, uint32_t *err)
             const unsigned long long t0 = global_ns();
             uint32_t spins = 0;
             while (gen.load(cuda::memory_order_acquire) == g) {
-                if ((++spins & 63u) == 0 && global_ns() - t0 > kGridWaitNs) {
+                if ((++spins & 63u) == 0 && global_ns() - t0 > wait_ns) {
                     set_error(err, kDevTimeout);
                     ok = 0;
                     break;
@@ -85,8 +85,12 @@ __device__ bool grid_barrier(CoreState *s, uint32_t *err)
 
 __global__ __launch_bounds__(kCoreThreads) void k_core_peel(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ cols,
-    uint32_t *cur, uint32_t *round_of, uint32_t *fa, uint32_t *fb, CoreState *s, uint32_t *err)
+    uint32_t *cur, uint32_t *round_of, uint32_t *fa, uint32_t *fb, CoreState *s, uint32_t *err,
+    unsigned long long wait_ns, uint32_t absent_block)
 {
+    // injected fault (tests only): this block never arrives at the first barrier, so that the
+    // other blocks' bounded wait there must run out
+    if (blockIdx.x == absent_block) return;
     const uint32_t nthreads = gridDim.x * blockDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31, gwarp = tid >> 5, nwarps = nthreads >> 5;
@@ -99,7 +103,7 @@ __global__ __launch_bounds__(kCoreThreads) void k_core_peel(
         round_of[v] = kPresent;
     }
     if (leader) s->gmin = kPresent;
-    if (!grid_barrier(s, err)) return;
+    if (!grid_barrier(s, err, wait_ns)) return;
 
     uint32_t t = 0, level = 0, removed = 0, f = 0;
     uint32_t *F = fa, *N = fb;
@@ -111,7 +115,7 @@ __global__ __launch_bounds__(kCoreThreads) void k_core_peel(
                 if (__ldcg(round_of + v) == kPresent) m = min(m, __ldcg(cur + v));
             m = __reduce_min_sync(kFull, m);
             if (lane == 0 && m != kPresent) atomicMin(&s->gmin, m);
-            if (!grid_barrier(s, err)) return;
+            if (!grid_barrier(s, err, wait_ns)) return;
             const uint32_t least = load_relaxed(&s->gmin);
             if (least == kPresent) {  // nothing left although removed < n: inconsistent input
                 set_error(err, kDevBadInput);
@@ -131,7 +135,7 @@ __global__ __launch_bounds__(kCoreThreads) void k_core_peel(
                     __stcg(round_of + v, t);
                 }
             }
-            if (!grid_barrier(s, err)) return;
+            if (!grid_barrier(s, err, wait_ns)) return;
             f = load_relaxed(&s->cnt[t % 3]);
             if (leader) s->gmin = kPresent;  // every block read it before the barrier above
             if (f == 0 || f > n - removed) {
@@ -168,7 +172,7 @@ __global__ __launch_bounds__(kCoreThreads) void k_core_peel(
                 }
             }
         }
-        if (!grid_barrier(s, err)) return;
+        if (!grid_barrier(s, err, wait_ns)) return;
         removed += f;
         t++;
         f = load_relaxed(&s->cnt[t % 3]);
@@ -230,7 +234,10 @@ cudaError_t launch_core_order(uint32_t n, uint64_t arcs, const uint64_t *off, co
     // One thread per vertex at most (fewer blocks make cheaper barriers), all blocks resident.
     uint32_t grid = (n + kCoreThreads - 1) / kCoreThreads;
     if (grid > (uint32_t)(num_sms * per_sm)) grid = (uint32_t)(num_sms * per_sm);
-    void *args[] = {&n, &arcs, &off, &cols, &cur, &round_of, &fa, &fb, &state, &err};
+    const citron_faults f = injected_faults();
+    unsigned long long wait_ns = f.barrier_wait_ns ? f.barrier_wait_ns : kGridWaitNs;
+    uint32_t absent = f.barrier_absent_block ? f.barrier_absent_block - 1 : 0xffffffffu;
+    void *args[] = {&n, &arcs, &off, &cols, &cur, &round_of, &fa, &fb, &state, &err, &wait_ns, &absent};
     e = cudaLaunchCooperativeKernel((const void *)k_core_peel, dim3(grid), dim3(kCoreThreads), args,
                                     0, st);
     note_launches(1);

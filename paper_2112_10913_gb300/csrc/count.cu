@@ -153,11 +153,28 @@ __global__ void k_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t
     if (u < n) per_root[u] = k == 1 ? 1ull : (unsigned long long)(dag_off[u + 1] - dag_off[u]);
 }
 
+// Sets count uint64 values (the injected seed of the device totals, tests only).
+__global__ void k_fill_u64(unsigned long long *p, uint32_t count, unsigned long long v)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) p[i] = v;
+}
+
 }  // namespace citron
 
 namespace citron_host {
 
 using namespace citron;
+
+// Seeds `count` device totals with the injected count_seed (no-op in normal operation).
+cudaError_t seed_totals(unsigned long long *p, uint32_t count, cudaStream_t s)
+{
+    const unsigned long long seed = injected_faults().count_seed;
+    if (!seed || !count) return cudaSuccess;
+    k_fill_u64<<<(count + 255) / 256, 256, 0, s>>>(p, count, seed);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 size_t count_ws_bytes(uint32_t n, uint32_t max_outdeg, int num_sms)
 {
@@ -201,6 +218,7 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
     cudaError_t e;
     if ((e = cudaMemsetAsync(st, 0, sizeof(CountStats), s))) return e;
     if ((e = cudaMemsetAsync(result, 0, 2 * sizeof(unsigned long long), s))) return e;
+    if ((e = seed_totals(result, 1, s))) return e;
     if ((e = cudaMemsetAsync(next, 0, 8 * sizeof(uint32_t), s))) return e;
     if ((e = cudaMemsetAsync(hist, 0, (kBitmapCap + 2) * sizeof(uint32_t), s))) return e;
     const uint32_t need = k - 1;

@@ -5,13 +5,11 @@
 //     ids enter in ascending order, so stability supplies the id tie-break.
 //   Algorithm GenOrdering (Sec. IV), fused into ONE pass over the arcs:
 //     k_tile_rows       : for every tile of 4096 arcs, the first vertex whose row starts in it;
-//     k_dag_compact<0>  : keep-test of every arc, block scan, decoupled look-back prefix over
+//     k_dag_compact     : keep-test of every arc, block scan, decoupled look-back prefix over
 //                         tiles, coalesced store of the kept arcs (the DAG columns, already sorted
 //                         per row) and of the DAG row offsets.  The count pass, PrefixSum and the
 //                         fill pass of the listing become one read of cols and one write of the DAG.
-//   Relabelled DAG from any rank (Sec. II directionalizing, rows renamed to ranks):
-//     k_dag_compact<1> (kept ranks, input row order) -> k_rl_rowlen -> k_scan_rowlen (look-back)
-//     -> k_rl_sort (per-row sort into rank order; k_rl_sort_long for rows above 512).
+//   The DAG of any rank, relabelled to ranks, is built in relabel.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -183,19 +181,16 @@ __global__ void k_degrees(uint32_t n, const uint64_t *__restrict__ off, uint32_t
     if (u < n) deg[u] = (uint32_t)min(off[u + 1] - off[u], (uint64_t)0xffffffffull);
 }
 
-// One pass over the arcs in tiles of 4096: keep-test of every arc, block scan, decoupled look-back
-// prefix over tiles, coalesced store of the kept values and of the row offsets.
-//   ORDER = 0 (Algorithm GenOrdering, Sec. IV): key = degree; u -> v kept iff
-//             (d(u), u) < (d(v), v); the kept value is v.  Rows keep the input's order.
-//   ORDER = 1 (any rank): key = rank; kept iff rank[v] > rank[u]; the kept value is rank[v]
-//             (rows stay in input order, unsorted: the relabel pass sorts them).
-// Every thread issues the key gathers of its 16 arcs before it uses any of them.
-template <int ORDER>
+// Algorithm GenOrdering (Sec. IV) in one pass over the arcs in tiles of 4096: keep-test of every
+// arc (u -> v kept iff (d(u), u) < (d(v), v), key = degree), block scan, decoupled look-back
+// prefix over tiles, coalesced store of the kept ids (rows keep the input's order, so they stay
+// sorted) and of the row offsets.  Every thread issues the key gathers of its 16 arcs before it
+// uses any of them.
 __global__ __launch_bounds__(kGoThreads) void k_dag_compact(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ cols,
     const uint32_t *__restrict__ key, const uint32_t *__restrict__ first_row, uint32_t ntiles,
     uint64_t *__restrict__ out_off, uint32_t *__restrict__ out_vals, uint64_t out_cap,
-    unsigned long long *status, uint32_t *ticket, uint32_t *err, int vec4)
+    unsigned long long *status, uint32_t *ticket, uint32_t *err, int vec4, WaitCfg wc)
 {
     __shared__ uint64_t s_row[kGoRowCap + 1];
     __shared__ uint32_t s_key[kGoRowCap + 1];
@@ -283,7 +278,7 @@ __global__ __launch_bounds__(kGoThreads) void k_dag_compact(
                     set_error(err, kDevBadInput);
                     continue;
                 }
-                const bool keep = ORDER == 0 ? (ku < kv[j] || (ku == kv[j] && r < w)) : (kv[j] > ku);
+                const bool keep = ku < kv[j] || (ku == kv[j] && r < w);
                 if (keep) mask |= 1u << j;
             }
         }
@@ -296,10 +291,10 @@ __global__ __launch_bounds__(kGoThreads) void k_dag_compact(
         uint32_t p = pref;
 #pragma unroll
         for (int j = 0; j < kGoItems; j++)
-            if (mask >> j & 1) s_out[p++] = ORDER == 0 ? v[j] : kv[j];
+            if (mask >> j & 1) s_out[p++] = v[j];
     }
     if (tid < 32) {
-        unsigned long long e = lookback_warp(status, t, total, err);
+        unsigned long long e = lookback_warp(status, t, total, err, wc);
         if (tid == 0) s_excl = e;
     }
     __syncthreads();
@@ -318,265 +313,6 @@ __global__ __launch_bounds__(kGoThreads) void k_dag_compact(
     }
     if (t == ntiles - 1) {  // trailing vertices whose rows start at the end of the arcs
         for (uint32_t u = first_row[ntiles] + tid; u <= n; u += kGoThreads) out_off[u] = excl + total;
-    }
-}
-
-// ------------------------------------------------------------------------------------------
-// Relabelled DAG from a rank permutation.
-
-// rowlen[rank[u]] = length of u's kept row (G[u+1] - G[u]); the largest goes to max_len.
-__global__ void k_rl_rowlen(uint32_t n, const uint64_t *__restrict__ G,
-                            const uint32_t *__restrict__ rank, uint32_t *__restrict__ rowlen,
-                            uint32_t *max_len, uint32_t *err)
-{
-    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t len = 0;
-    if (u < n) {
-        const uint32_t ru = rank[u];
-        len = (uint32_t)min(G[u + 1] - G[u], (uint64_t)0xffffffffull);
-        if (ru < n) rowlen[ru] = len;
-        else set_error(err, kDevBadInput);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(kFull, len, o));
-    if ((threadIdx.x & 31) == 0 && len) atomicMax(max_len, len);
-}
-
-constexpr int kScThreads = 256;
-constexpr int kScItems = 16;
-constexpr uint32_t kScTile = kScThreads * kScItems;
-
-// dag_off[i] = sum of rowlen[0..i), dag_off[n] = total; single pass with look-back.
-__global__ __launch_bounds__(kScThreads) void k_scan_rowlen(uint32_t n, const uint32_t *rowlen,
-                                                            uint64_t *dag_off, uint32_t ntiles,
-                                                            unsigned long long *status,
-                                                            uint32_t *ticket, uint32_t *err)
-{
-    __shared__ uint32_t s_scan[kScThreads / 32 + 1];
-    __shared__ uint32_t s_tile;
-    __shared__ unsigned long long s_excl;
-    const int tid = threadIdx.x;
-    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t t = s_tile;
-    if (t >= ntiles) return;
-    const uint64_t i0 = (uint64_t)t * kScTile + (uint64_t)tid * kScItems;
-    uint32_t v[kScItems];
-    uint32_t s = 0;
-#pragma unroll
-    for (int j = 0; j < kScItems; j++) {
-        v[j] = (i0 + j < n) ? rowlen[i0 + j] : 0;
-        s += v[j];
-    }
-    uint32_t total;
-    const uint32_t pref = block_excl_scan(s, s_scan, total);
-    if (tid < 32) {
-        unsigned long long e = lookback_warp(status, t, total, err);
-        if (tid == 0) s_excl = e;
-    }
-    __syncthreads();
-    unsigned long long run = s_excl + pref;
-#pragma unroll
-    for (int j = 0; j < kScItems; j++) {
-        if (i0 + j < n) dag_off[i0 + j] = run;
-        run += v[j];
-    }
-    if (t == ntiles - 1 && tid == kScThreads - 1) dag_off[n] = run;
-}
-
-// Bitonic sort of a power-of-two buffer in shared memory by one warp (or one block when
-// `block` is set).
-__device__ __forceinline__ void bitonic_smem(uint32_t *s, uint32_t p, int lane, int width,
-                                             bool block)
-{
-    for (uint32_t k = 2; k <= p; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = lane; i < p; i += width) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint32_t a = s[i], b = s[ixj];
-                    const bool asc = (i & k) == 0;
-                    if ((a > b) == asc) {
-                        s[i] = b;
-                        s[ixj] = a;
-                    }
-                }
-            }
-            if (block) __syncthreads();
-            else __syncwarp();
-        }
-    }
-}
-
-// Ascending bitonic sort of 32*E values held by one warp in registers, striped: value e of
-// lane l has index e*32 + l.  Partners closer than 32 are on other lanes (shuffles), farther
-// ones are in the same lane's registers.
-template <int E>
-__device__ __forceinline__ void warp_sort_striped(uint32_t (&v)[E], int lane)
-{
-#pragma unroll
-    for (int k = 2; k <= 32 * E; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int je = j >> 5;
-#pragma unroll
-                for (int e = 0; e < E; e++) {
-                    if ((e & je) == 0) {
-                        const int e2 = e | je;
-                        const bool asc = (((uint32_t)(e * 32 + lane)) & k) == 0;
-                        const uint32_t a = v[e], b = v[e2];
-                        const bool sw = (a > b) == asc;
-                        v[e] = sw ? b : a;
-                        v[e2] = sw ? a : b;
-                    }
-                }
-            } else {
-                const bool lower = (lane & j) == 0;
-#pragma unroll
-                for (int e = 0; e < E; e++) {
-                    const bool asc = (((uint32_t)(e * 32 + lane)) & k) == 0;
-                    const uint32_t q = __shfl_xor_sync(kFull, v[e], j);
-                    v[e] = (lower == asc) ? min(v[e], q) : max(v[e], q);
-                }
-            }
-        }
-    }
-}
-
-// Loads a row of len <= 32*E values (striped, padded with the maximum), sorts it in registers
-// and stores it to dst.
-template <int E>
-__device__ __forceinline__ void warp_sort_row(const uint32_t *src, uint32_t len, uint32_t *dst, int lane)
-{
-    uint32_t v[E];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const uint32_t i = e * 32 + lane;
-        v[e] = i < len ? src[i] : 0xffffffffu;
-    }
-    warp_sort_striped<E>(v, lane);
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const uint32_t i = e * 32 + lane;
-        if (i < len) dst[i] = v[e];
-    }
-}
-
-constexpr int kRlWarps = 8;
-constexpr uint32_t kRlRows = 256;     // rows per block step
-constexpr uint32_t kRlStage = 8192;   // kept entries staged in shared memory per step
-constexpr uint32_t kRlWarpCap = 512;  // rows up to this length are sorted by one warp
-constexpr uint32_t kLongCap = 32768;  // longest relabelled row this build sorts (power of 2)
-
-// Relabel: the kept row of input vertex u (values = ranks, input order) becomes row rank[u] of
-// the DAG, sorted.  A block takes 256 consecutive input rows at a time.  Their offsets, ranks and
-// destinations are staged in shared memory (coalesced, independent loads) and, when the rows'
-// entries fit, the entries too (one coalesced copy: the rows are contiguous).  Rows of at most
-// 32 entries are then sorted with one thread per entry: its place is the number of smaller
-// entries in its row (ranks are distinct).  Rows up to 512 entries are sorted by one warp in
-// registers (bitonic, up to 16 values per lane); longer rows are listed for k_rl_sort_long.
-__global__ __launch_bounds__(kRlWarps * 32) void k_rl_sort(
-    uint32_t n, const uint64_t *__restrict__ G, const uint32_t *__restrict__ vals,
-    const uint32_t *__restrict__ rank, const uint64_t *__restrict__ dag_off,
-    uint32_t *__restrict__ dag_cols, uint64_t dag_cap, uint32_t *long_rows, uint32_t *n_long,
-    uint32_t *err)
-{
-    __shared__ uint64_t s_g[kRlRows + 1];
-    __shared__ uint64_t s_dst[kRlRows];
-    __shared__ uint32_t s_vals[kRlStage];
-    __shared__ uint8_t s_rowid[kRlStage];  // row (within the step) of each staged entry of a short row
-    static_assert(kRlRows <= 256, "row ids are 8-bit");
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (uint32_t r0 = blockIdx.x * kRlRows; r0 < n; r0 += gridDim.x * kRlRows) {
-        const uint32_t cnt = min(kRlRows, n - r0);
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i <= cnt; i += blockDim.x) s_g[i] = G[r0 + i];
-        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-            const uint32_t ru = rank[r0 + i];
-            s_dst[i] = ru < n ? dag_off[ru] : ~0ull;
-        }
-        __syncthreads();
-        const uint64_t base = s_g[0];
-        const uint64_t total = s_g[cnt] - base;
-        const bool staged = total <= kRlStage;
-        if (staged) {
-            for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) s_vals[i] = vals[base + i];
-            for (uint32_t i = w; i < cnt; i += kRlWarps) {  // row ids of the short rows' entries
-                const uint32_t rb = (uint32_t)(s_g[i] - base), re = (uint32_t)(s_g[i + 1] - base);
-                if (re - rb <= 32 && rb + lane < re) s_rowid[rb + lane] = (uint8_t)i;
-            }
-        }
-        __syncthreads();
-        // short rows: one thread per staged entry
-        if (staged) {
-            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                // entries of long rows hold a stale id: the range check sends them to the warps
-                const uint32_t lo = s_rowid[e];
-                if (lo >= cnt) continue;
-                const uint32_t rb = (uint32_t)(s_g[lo] - base), len = (uint32_t)(s_g[lo + 1] - s_g[lo]);
-                if (e < rb || e >= rb + len || len > 32) continue;
-                const uint64_t dst = s_dst[lo];
-                if (dst == ~0ull || dst + len > dag_cap) {
-                    set_error(err, kDevBadInput);
-                    continue;
-                }
-                const uint32_t x = s_vals[e];
-                uint32_t pos = 0;
-                for (uint32_t j = 0; j < len; j++) pos += s_vals[rb + j] < x;
-                dag_cols[dst + pos] = x;
-            }
-        }
-        // longer rows (and every row of a step whose entries were not staged): one warp each
-        for (uint32_t i = w; i < cnt; i += kRlWarps) {
-            const uint64_t b = s_g[i];
-            const uint32_t len = (uint32_t)(s_g[i + 1] - b);
-            if (len == 0 || (staged && len <= 32)) continue;
-            const uint64_t dst = s_dst[i];
-            if (dst == ~0ull || dst + len > dag_cap) {
-                if (lane == 0) set_error(err, kDevBadInput);
-                continue;
-            }
-            const uint32_t *src = staged ? s_vals + (b - base) : vals + b;
-            uint32_t *out = dag_cols + dst;
-            if (len <= 32) warp_sort_row<1>(src, len, out, lane);
-            else if (len <= 64) warp_sort_row<2>(src, len, out, lane);
-            else if (len <= 128) warp_sort_row<4>(src, len, out, lane);
-            else if (len <= 256) warp_sort_row<8>(src, len, out, lane);
-            else if (len <= kRlWarpCap) warp_sort_row<16>(src, len, out, lane);
-            else if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = r0 + i;
-        }
-    }
-}
-
-// One block per long row; dynamic shared memory holds the padded row.
-__global__ __launch_bounds__(1024) void k_rl_sort_long(
-    uint32_t n, const uint64_t *__restrict__ G, const uint32_t *__restrict__ vals,
-    const uint32_t *__restrict__ rank, const uint64_t *__restrict__ dag_off,
-    uint32_t *__restrict__ dag_cols, uint64_t dag_cap, const uint32_t *long_rows,
-    const uint32_t *n_long, uint32_t cap, uint32_t *err)
-{
-    extern __shared__ uint32_t s_row[];
-    for (uint32_t it = blockIdx.x; it < *n_long; it += gridDim.x) {
-        const uint32_t u = long_rows[it];
-        const uint32_t ru = rank[u];
-        const uint64_t b = G[u];
-        const uint32_t len = (uint32_t)(G[u + 1] - b);
-        if (len > cap || ru >= n) {
-            if (threadIdx.x == 0) set_error(err, len > cap ? kDevTooLong : kDevBadInput);
-            continue;
-        }
-        uint32_t p = 64;
-        while (p < len) p <<= 1;
-        for (uint32_t j = threadIdx.x; j < p; j += blockDim.x) s_row[j] = j < len ? vals[b + j] : 0xffffffffu;
-        __syncthreads();
-        bitonic_smem(s_row, p, threadIdx.x, blockDim.x, true);
-        const uint64_t dst = dag_off[ru];
-        if (dst + len <= dag_cap)
-            for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) dag_cols[dst + j] = s_row[j];
-        else if (threadIdx.x == 0)
-            set_error(err, kDevBadInput);
-        __syncthreads();
     }
 }
 
@@ -696,6 +432,12 @@ cudaError_t launch_rank_by_key(uint32_t n, const uint32_t *keys, uint32_t key_bo
     return sort_ids(n, nullptr, keys, radix_passes(key_bound ? key_bound : 1), rank, perm, c, st);
 }
 
+size_t relabel_ws_bytes(uint32_t n, uint64_t arcs);
+cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, const uint32_t *cols,
+                               const uint32_t *rank, uint64_t *dag_off, uint32_t *dag_cols,
+                               uint32_t *d_max_outdeg, uint32_t *err, Carver &c, cudaStream_t st,
+                               int num_sms);
+
 size_t dag_ws_bytes(uint32_t n, uint64_t arcs)
 {
     Sizer s;
@@ -703,12 +445,17 @@ size_t dag_ws_bytes(uint32_t n, uint64_t arcs)
     s.take<uint32_t>(ntiles + 2);             // first_row
     s.take<unsigned long long>(ntiles + 1);   // look-back status (compaction)
     s.take<uint32_t>(8);                      // tickets, counters
-    s.take<uint32_t>((size_t)n + 1);          // degrees / rowlen
-    s.take<unsigned long long>((size_t)n / kScTile + 2);  // look-back status (scan)
-    s.take<uint32_t>((size_t)n + 1);          // long rows
-    s.take<uint64_t>((size_t)n + 1);          // kept-row offsets in input order
-    s.take<uint32_t>(arcs / 2 + 1);           // kept ranks in input order
-    return s.used;
+    s.take<uint32_t>((size_t)n + 1);          // degrees
+    const size_t r = relabel_ws_bytes(n, arcs);
+    return r > s.used ? r : s.used;
+}
+
+cudaError_t launch_tile_rows(uint32_t n, uint64_t arcs, const uint64_t *off, uint32_t tile,
+                             uint32_t ntiles, uint32_t *first_row, cudaStream_t st)
+{
+    k_tile_rows<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, arcs, off, tile, ntiles, first_row);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 // Returns cudaErrorMemoryAllocation if the workspace is short; device errors land in err.
@@ -717,17 +464,16 @@ cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, con
                              uint32_t *d_max_outdeg, uint32_t *err, Carver &c, cudaStream_t st,
                              int num_sms)
 {
+    if (rank)
+        return launch_relabel_dag(n, arcs, off, cols, rank, dag_off, dag_cols, d_max_outdeg, err, c,
+                                  st, num_sms);
     const uint64_t ntiles64 = (arcs + kGoTile - 1) / kGoTile;
     uint32_t *first_row = c.take<uint32_t>(ntiles64 + 2);
     unsigned long long *status = c.take<unsigned long long>(ntiles64 + 1);
     uint32_t *ctr = c.take<uint32_t>(8);
     uint32_t *keys = c.take<uint32_t>((size_t)n + 1);
-    const uint32_t sc_tiles = (n + kScTile - 1) / kScTile;
-    unsigned long long *sc_status = c.take<unsigned long long>((size_t)n / kScTile + 2);
-    uint32_t *long_rows = c.take<uint32_t>((size_t)n + 1);
-    uint64_t *G = c.take<uint64_t>((size_t)n + 1);
-    uint32_t *kept = c.take<uint32_t>(arcs / 2 + 1);
     if (!c.ok) return cudaErrorMemoryAllocation;
+    if (ntiles64 >= 0xffffffffull) return cudaErrorInvalidValue;
     cudaError_t e;
     if ((e = cudaMemsetAsync(ctr, 0, 8 * sizeof(uint32_t), st))) return e;
     if (arcs == 0 || n == 0) {
@@ -736,44 +482,15 @@ cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, con
     const uint32_t ntiles = (uint32_t)ntiles64;
     const int vec4 = ((uintptr_t)cols % 16) == 0;
     if ((e = cudaMemsetAsync(status, 0, ntiles64 * sizeof(unsigned long long), st))) return e;
-    k_tile_rows<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, arcs, off, kGoTile, ntiles, first_row);
-    note_launches(1);
-    if (!rank) {
-        k_degrees<<<(n + 255) / 256, 256, 0, st>>>(n, off, keys);
-        k_dag_compact<0><<<ntiles, kGoThreads, 0, st>>>(n, arcs, off, cols, keys, first_row, ntiles,
-                                                       dag_off, dag_cols, arcs / 2, status, ctr,
-                                                       err, vec4);
-        note_launches(2);
-        if (d_max_outdeg) {
-            k_max_rowlen<<<num_sms * 4, 256, 0, st>>>(n, dag_off, d_max_outdeg);
-            note_launches(1);
-        }
-        return cudaGetLastError();
+    if ((e = launch_tile_rows(n, arcs, off, kGoTile, ntiles, first_row, st))) return e;
+    k_degrees<<<(n + 255) / 256, 256, 0, st>>>(n, off, keys);
+    k_dag_compact<<<ntiles, kGoThreads, 0, st>>>(n, arcs, off, cols, keys, first_row, ntiles, dag_off,
+                                                 dag_cols, arcs / 2, status, ctr, err, vec4, wait_cfg());
+    note_launches(2);
+    if (d_max_outdeg) {
+        k_max_rowlen<<<num_sms * 4, 256, 0, st>>>(n, dag_off, d_max_outdeg);
+        note_launches(1);
     }
-    if ((e = cudaMemsetAsync(sc_status, 0, ((size_t)sc_tiles + 1) * sizeof(unsigned long long), st)))
-        return e;
-    if ((e = cudaMemsetAsync(keys, 0, ((size_t)n + 1) * sizeof(uint32_t), st))) return e;
-    uint32_t *max_len = ctr + 2;
-    uint32_t *n_long = ctr + 3;
-    k_dag_compact<1><<<ntiles, kGoThreads, 0, st>>>(n, arcs, off, cols, rank, first_row, ntiles, G,
-                                                   kept, arcs / 2, status, ctr, err, vec4);
-    k_rl_rowlen<<<(n + 255) / 256, 256, 0, st>>>(n, G, rank, keys, max_len, err);
-    k_scan_rowlen<<<sc_tiles, kScThreads, 0, st>>>(n, keys, dag_off, sc_tiles, sc_status, ctr + 1,
-                                                   err);
-    uint32_t rl_grid = (n + kRlRows - 1) / kRlRows;
-    if (rl_grid > (uint32_t)num_sms * 6) rl_grid = (uint32_t)num_sms * 6;
-    k_rl_sort<<<rl_grid, kRlWarps * 32, 0, st>>>(n, G, kept, rank, dag_off, dag_cols, arcs / 2,
-                                                 long_rows, n_long, err);
-    const uint32_t cap_bytes = kLongCap * sizeof(uint32_t);
-    if ((e = cudaFuncSetAttribute(k_rl_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  cap_bytes)))
-        return e;
-    k_rl_sort_long<<<num_sms, 1024, cap_bytes, st>>>(n, G, kept, rank, dag_off, dag_cols, arcs / 2,
-                                                     long_rows, n_long, kLongCap, err);
-    note_launches(5);
-    if (d_max_outdeg)
-        if ((e = cudaMemcpyAsync(d_max_outdeg, max_len, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)))
-            return e;
     return cudaGetLastError();
 }
 
