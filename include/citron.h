@@ -231,6 +231,17 @@ citron_status citron_count_batch(uint32_t n, const uint64_t *d_dag_off, const ui
 citron_status citron_workspace_status(void *ws, void *stream);
 
 /*
+ * citron_probe_word_ops -- measures the device's peak rate of the counting phase's unit of work,
+ * the 32-bit word operation (one AND, one POPC and one add on register operands), for the
+ * roofline of the counting kernels (the paper has no counterpart: this is measurement).  A
+ * kernel of blocks_per_sm x (number of SMs) blocks of 1024 threads runs `iters` iterations of 8
+ * independent word operations per thread; *h_ops_per_s receives word operations per second and
+ * *h_ms the kernel's device time (CUDA events on `stream`).  Synchronises `stream`.
+ */
+citron_status citron_probe_word_ops(uint32_t blocks_per_sm, uint32_t iters, double *h_ops_per_s,
+                                    float *h_ms, void *stream);
+
+/*
  * citron_set_faults -- fault injection for tests of the error paths (the paper has no
  * counterpart: the method itself never fails).  Process-wide; applies to every call made after it
  * on any device until it is called again; NULL restores normal operation.  Nothing here faults

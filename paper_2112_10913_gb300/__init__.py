@@ -45,6 +45,7 @@ EXPORTS = (
     "citron_count_batch",
     "citron_workspace_status",
     "citron_set_faults",
+    "citron_probe_word_ops",
 )
 
 COUNT_TIME_KERNELS = 1
@@ -134,6 +135,8 @@ def lib() -> ctypes.CDLL:
     L.citron_workspace_status.restype = i32
     L.citron_set_faults.argtypes = [vp]
     L.citron_set_faults.restype = i32
+    L.citron_probe_word_ops.argtypes = [u32, u32, vp, vp, vp]
+    L.citron_probe_word_ops.restype = i32
     _lib = L
     return L
 
@@ -268,6 +271,14 @@ def citron_set_faults(lookback_spin_limit: int = 0, lookback_stall_tile: int | N
     clear = not any((lookback_spin_limit, lookback_stall_tile is not None, barrier_wait_ns,
                      barrier_absent_block is not None, count_seed))
     _check(lib().citron_set_faults(None if clear else ctypes.byref(f)), "citron_set_faults")
+
+
+def citron_probe_word_ops(blocks_per_sm: int = 2, iters: int = 200000, stream=None) -> tuple[float, float]:
+    """Measured peak of 32-bit word operations (AND + POPC + add) per second, and its kernel ms."""
+    ops, ms = ctypes.c_double(0), ctypes.c_float(0)
+    _check(lib().citron_probe_word_ops(blocks_per_sm, iters, ctypes.byref(ops), ctypes.byref(ms),
+                                       _stream(stream)), "citron_probe_word_ops")
+    return float(ops.value), float(ms.value)
 
 
 def citron_workspace_status(ws, stream=None):

@@ -197,7 +197,7 @@ namespace citron_host {
 using namespace citron;
 
 cudaError_t launch_rank_by_key(uint32_t n, const uint32_t *keys, uint32_t key_bound, uint32_t *rank,
-                               uint32_t *perm, Carver &c, cudaStream_t st);
+                               uint32_t *perm, uint32_t *err, Carver &c, cudaStream_t st);
 size_t order_ws_bytes(uint32_t n);
 
 size_t core_ws_bytes(uint32_t n)
@@ -251,7 +251,7 @@ cudaError_t launch_core_order(uint32_t n, uint64_t arcs, const uint64_t *off, co
     if (code) return cudaSuccess;  // reported from the error word by the caller
     if (h_level) *h_level = hs.level;
     if (h_rounds) *h_rounds = hs.rounds;
-    return launch_rank_by_key(n, round_of, hs.rounds, rank, perm, c, st);
+    return launch_rank_by_key(n, round_of, hs.rounds, rank, perm, err, c, st);
 }
 
 }  // namespace citron_host

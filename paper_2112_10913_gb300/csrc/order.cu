@@ -1,8 +1,7 @@
 // order.cu -- ordering phase on sm_103a: degree ordering, DAG construction, input validation.
 //
-//   Degree ordering (Sec. II, Sec. IV): rank = position of u when sorted by (d(u), u).
-//     k_radix_hist / k_radix_scatter: stable LSD radix sort of the ids by degree, 8-bit digits;
-//     ids enter in ascending order, so stability supplies the id tie-break.
+//   Degree ordering (Sec. II, Sec. IV): rank = position of u when sorted by (d(u), u), by the
+//     single-sweep radix sort of sort.cu.
 //   Algorithm GenOrdering (Sec. IV), fused into ONE pass over the arcs:
 //     k_tile_rows       : for every tile of 4096 arcs, the first vertex whose row starts in it;
 //     k_dag_compact     : keep-test of every arc, block scan, decoupled look-back prefix over
@@ -16,138 +15,6 @@
 #include "common.cuh"
 
 namespace citron {
-
-// ------------------------------------------------------------------------------------------
-// Radix sort of vertex ids by degree.
-
-constexpr int kRsThreads = 256;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 4096 keys per block
-
-__device__ __forceinline__ uint32_t degree_of(const uint64_t *off, uint32_t u)
-{
-    return (uint32_t)(off[u + 1] - off[u]);
-}
-
-// Per-block histogram of one 8-bit digit.  hist is digit-major: hist[d * nblocks + b].
-__global__ __launch_bounds__(kRsThreads) void k_radix_hist(const uint64_t *off, const uint32_t *keys,
-                                                           uint32_t n, int shift, uint32_t *hist,
-                                                           uint32_t nblocks)
-{
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t base = blockIdx.x * kRsTile;
-#pragma unroll 4
-    for (int i = 0; i < kRsItems; i++) {
-        uint32_t idx = base + i * kRsThreads + threadIdx.x;
-        if (idx < n) {
-            uint32_t key = keys ? keys[idx] : degree_of(off, idx);
-            atomicAdd(&cnt[(key >> shift) & 255u], 1u);
-        }
-    }
-    __syncthreads();
-    hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
-}
-
-// Exclusive scan of one uint32 array by a single block of 1024 threads (sizes here are
-// 256 x blocks).  Each warp owns one contiguous segment and walks it 32 entries at a time, so
-// every load and store is coalesced.
-__global__ __launch_bounds__(1024) void k_scan_small(uint32_t *data, uint32_t count)
-{
-    __shared__ uint32_t s_warp[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t seg = ((count + 31) / 32 + 31) & ~31u;
-    const uint32_t lo = min(count, (uint32_t)w * seg), hi = min(count, lo + seg);
-    constexpr int kBatch = 8;  // loads of one lane in flight together
-    uint32_t sum = 0;
-    for (uint32_t b = lo; b < hi; b += 32 * kBatch) {
-        uint32_t v[kBatch];
-#pragma unroll
-        for (int t = 0; t < kBatch; t++) {
-            const uint32_t i = b + t * 32 + lane;
-            v[t] = i < hi ? data[i] : 0u;
-        }
-#pragma unroll
-        for (int t = 0; t < kBatch; t++) sum += v[t];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-    if (lane == 0) s_warp[w] = sum;
-    __syncthreads();
-    if (w == 0) {
-        const uint32_t v = s_warp[lane];
-        const uint32_t incl = warp_incl_scan(v);
-        s_warp[lane] = incl - v;
-    }
-    __syncthreads();
-    uint32_t carry = s_warp[w];
-    for (uint32_t b = lo; b < hi; b += 32 * kBatch) {
-        uint32_t v[kBatch];
-#pragma unroll
-        for (int t = 0; t < kBatch; t++) {
-            const uint32_t i = b + t * 32 + lane;
-            v[t] = i < hi ? data[i] : 0u;
-        }
-#pragma unroll
-        for (int t = 0; t < kBatch; t++) {
-            const uint32_t i = b + t * 32 + lane;
-            const uint32_t incl = warp_incl_scan(v[t]);
-            if (i < hi) data[i] = carry + incl - v[t];
-            carry += __shfl_sync(kFull, incl, 31);
-        }
-    }
-}
-
-// Stable scatter of one digit.  Keys of a tile are visited in index order (round-major,
-// thread-minor); ranks inside a round come from __match_any_sync peers and a per-digit prefix
-// over the warps.  On the last pass the permutation and the rank array are written.
-__global__ __launch_bounds__(kRsThreads) void k_radix_scatter(
-    const uint64_t *off, const uint32_t *keys_in, const uint32_t *vals_in, uint32_t n, int shift,
-    const uint32_t *hist, uint32_t nblocks, uint32_t *keys_out, uint32_t *vals_out,
-    uint32_t *rank_out)
-{
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wcnt[kRsThreads / 32][256];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    base[tid] = hist[tid * nblocks + blockIdx.x];
-    const uint32_t tile = blockIdx.x * kRsTile;
-    for (int r = 0; r < kRsItems; r++) {
-#pragma unroll
-        for (int w = 0; w < kRsThreads / 32; w++) wcnt[w][tid] = 0;
-        __syncthreads();
-        const uint32_t idx = tile + r * kRsThreads + tid;
-        const bool valid = idx < n;
-        uint32_t key = 0, val = 0, d = 256;
-        if (valid) {
-            key = keys_in ? keys_in[idx] : degree_of(off, idx);
-            val = vals_in ? vals_in[idx] : idx;
-            d = (key >> shift) & 255u;
-        }
-        const uint32_t peers = __match_any_sync(kFull, d);
-        const uint32_t lrank = __popc(peers & lanemask_lt());
-        if (valid && lrank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {  // thread tid owns digit tid: exclusive prefix over warps, plus the running base
-            uint32_t run = base[tid];
-#pragma unroll
-            for (int w = 0; w < kRsThreads / 32; w++) {
-                uint32_t c = wcnt[w][tid];
-                wcnt[w][tid] = run;
-                run += c;
-            }
-            base[tid] = run;
-        }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = wcnt[warp][d] + lrank;
-            if (keys_out) keys_out[pos] = key;
-            vals_out[pos] = val;
-            if (rank_out) rank_out[val] = pos;
-        }
-        __syncthreads();
-    }
-}
 
 // ------------------------------------------------------------------------------------------
 // Algorithm GenOrdering, fused.
@@ -372,65 +239,6 @@ __global__ void k_max_rowlen(uint32_t n, const uint64_t *off, uint32_t *out)
 namespace citron_host {
 
 using namespace citron;
-
-size_t order_ws_bytes(uint32_t n)
-{
-    Sizer s;
-    const uint32_t nb = (n + kRsTile - 1) / kRsTile + 1;
-    s.take<uint32_t>((size_t)n);        // keys ping
-    s.take<uint32_t>((size_t)n);        // keys pong
-    s.take<uint32_t>((size_t)n);        // vals ping
-    s.take<uint32_t>((size_t)n);        // vals pong
-    s.take<uint32_t>((size_t)256 * nb);  // histogram
-    return s.used;
-}
-
-static int radix_passes(uint32_t n)
-{
-    int bits = 0;
-    while (bits < 32 && ((uint64_t)(n ? n - 1 : 0) >> bits) != 0) bits++;
-    return bits <= 8 ? 1 : (bits + 7) / 8;
-}
-
-// Stable LSD sort of the ids 0..n-1 by a key: the degree (keys0 == NULL) or keys0[id].  Writes
-// rank[id] = position and, when perm != NULL, perm[position] = id.  `passes` 8-bit digits.
-static cudaError_t sort_ids(uint32_t n, const uint64_t *off, const uint32_t *keys0, int passes,
-                            uint32_t *rank, uint32_t *perm, Carver &c, cudaStream_t st)
-{
-    const uint32_t nb = (n + kRsTile - 1) / kRsTile;
-    uint32_t *keys[2] = {c.take<uint32_t>(n), c.take<uint32_t>(n)};
-    uint32_t *vals[2] = {c.take<uint32_t>(n), c.take<uint32_t>(n)};
-    uint32_t *hist = c.take<uint32_t>((size_t)256 * (nb + 1));
-    if (!c.ok) return cudaErrorMemoryAllocation;
-    if (n == 0) return cudaSuccess;
-    const uint32_t *kin = keys0, *vin = nullptr;
-    for (int p = 0; p < passes; p++) {
-        const bool last = p == passes - 1;
-        k_radix_hist<<<nb, kRsThreads, 0, st>>>(off, kin, n, 8 * p, hist, nb);
-        k_scan_small<<<1, 1024, 0, st>>>(hist, 256 * nb);
-        uint32_t *kout = last ? nullptr : keys[p & 1];
-        uint32_t *vout = last ? (perm ? perm : vals[p & 1]) : vals[p & 1];
-        k_radix_scatter<<<nb, kRsThreads, 0, st>>>(off, kin, vin, n, 8 * p, hist, nb, kout, vout,
-                                                   last ? rank : nullptr);
-        note_launches(3);
-        kin = kout;
-        vin = vout;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_order(uint32_t n, const uint64_t *off, uint32_t *rank, uint32_t *perm,
-                         Carver &c, cudaStream_t st)
-{
-    return sort_ids(n, off, nullptr, radix_passes(n), rank, perm, c, st);
-}
-
-// Ranks by (key, id) for keys below key_bound (the core ordering's removal rounds).
-cudaError_t launch_rank_by_key(uint32_t n, const uint32_t *keys, uint32_t key_bound, uint32_t *rank,
-                               uint32_t *perm, Carver &c, cudaStream_t st)
-{
-    return sort_ids(n, nullptr, keys, radix_passes(key_bound ? key_bound : 1), rank, perm, c, st);
-}
 
 size_t relabel_ws_bytes(uint32_t n, uint64_t arcs);
 cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, const uint32_t *cols,

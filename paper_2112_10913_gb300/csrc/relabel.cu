@@ -59,23 +59,69 @@ __device__ __forceinline__ uint32_t tile_prefix(const uint32_t *s_pref, const ui
     return s_pref[q] + __popc((uint32_t)s_mask[q] & ((1u << b) - 1u));
 }
 
-// first_row[b] = min{u : off[u] >= b * 4096} (k_tile_rows, order.cu).
+// Rows of a tile with more than kKeRowCap rows (long runs of empty rows): every kept arc takes
+// its place in its row with its own atomic.  Offsets are read from global memory.
+__device__ __noinline__ void rl_keep_uncached(uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off,
+                                              const uint32_t *__restrict__ cols,
+                                              const uint32_t *__restrict__ rank, uint32_t r0,
+                                              uint32_t u_next, uint64_t t0, uint64_t t1,
+                                              uint32_t *kept, uint32_t *rowlen, uint32_t *err)
+{
+    const uint64_t a0 = t0 + (uint64_t)threadIdx.x * kKeItems;
+    if (a0 >= t1) return;
+    uint32_t lo = r0, hi = u_next;  // last r with off[r] <= a0
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo + 1) / 2;
+        if (off[mid] <= a0) lo = mid;
+        else hi = mid - 1;
+    }
+    uint32_t r = lo;
+    uint64_t rs = off[r], re = off[r + 1];
+    for (int j = 0; j < kKeItems; j++) {
+        const uint64_t a = a0 + j;
+        if (a >= t1) break;
+        while (re <= a && r + 1 < u_next) {
+            r++;
+            rs = re;
+            re = off[r + 1];
+        }
+        const uint32_t v = cols[a];
+        const uint32_t ku = rank[r];
+        if (v >= n || ku >= n || rs > re || re > arcs) {
+            set_error(err, kDevBadInput);
+            continue;
+        }
+        const uint32_t kv = rank[v];
+        if (kv > ku) {
+            const uint32_t pos = atomicAdd(&rowlen[ku], 1u);
+            if (pos < re - rs) kept[rs + pos] = kv;
+            else set_error(err, kDevBadInput);
+        }
+    }
+}
+
+// first_row[b] = min{u : off[u] >= b * 4096} (k_tile_rows, order.cu).  Positions inside a tile
+// are 32-bit offsets from its first arc t0; the tile's rows are cached with their starts
+// clamped to the tile.
 __global__ __launch_bounds__(kKeThreads) void k_rl_keep(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ cols,
     const uint32_t *__restrict__ rank, const uint32_t *__restrict__ first_row, uint32_t *kept,
     uint32_t *rowlen, uint32_t *err, int vec4)
 {
-    __shared__ uint64_t s_row[kKeRowCap + 1];
-    __shared__ uint32_t s_key[kKeRowCap + 1];
+    __shared__ uint32_t s_rel[kKeRowCap + 1];  // row starts - t0, clamped to [0, len]
+    __shared__ uint32_t s_key[kKeRowCap];      // rank of each row
+    __shared__ int32_t s_delta[kKeRowCap];     // place of the row's piece minus P(piece start)
+    __shared__ uint32_t s_out[kKeTile];        // kept ranks in tile order
+    __shared__ uint16_t s_krow[kKeTile];       // tile row of each kept rank
     __shared__ uint32_t s_pref[kKeThreads + 1];
     __shared__ uint16_t s_mask[kKeThreads];
-    __shared__ int32_t s_delta[kKeTile];
     __shared__ uint32_t s_scan[kKeThreads / 32 + 1];
 
     const int tid = threadIdx.x;
     const uint32_t t = blockIdx.x;
     const uint64_t t0 = (uint64_t)t * kKeTile;
     const uint64_t t1 = min(t0 + kKeTile, arcs);
+    const uint32_t len = (uint32_t)(t1 - t0);
     const uint32_t u_first = first_row[t];
     const uint32_t u_next = first_row[t + 1];
     const bool bad = u_first > n || u_next > n || u_next < u_first || (t > 0 && u_first == 0);
@@ -84,23 +130,25 @@ __global__ __launch_bounds__(kKeThreads) void k_rl_keep(
         return;
     }
     // rows r0 .. u_next-1 can hold arcs of this tile (r0 = last row starting at or before t0)
-    const uint32_t r0 = (off[u_first] == t0) ? u_first : u_first - 1;
+    const uint64_t o_first = off[u_first];
+    const uint32_t r0 = (o_first == t0) ? u_first : u_first - 1;
     const uint32_t nrows = u_next - r0;
-    const bool cached = nrows + 1 <= kKeRowCap + 1;
-    if (cached) {
-        for (uint32_t i = tid; i <= nrows; i += kKeThreads) {
-            s_row[i] = off[r0 + i];
-            s_key[i] = (r0 + i < n) ? rank[r0 + i] : 0u;
-        }
+    if (nrows > kKeRowCap || nrows == 0) {
+        rl_keep_uncached(n, arcs, off, cols, rank, r0, u_next, t0, t1, kept, rowlen, err);
+        return;
+    }
+    const uint64_t row0_start = off[r0];
+    for (uint32_t i = tid; i <= nrows; i += kKeThreads) {
+        const uint64_t o = off[r0 + i];
+        s_rel[i] = o <= t0 ? 0u : (o - t0 >= len ? len : (uint32_t)(o - t0));
+        if (i < nrows) s_key[i] = rank[r0 + i];
     }
     __syncthreads();
-    auto row_start = [&](uint32_t r) -> uint64_t { return cached ? s_row[r - r0] : off[r]; };
-    auto row_key = [&](uint32_t r) -> uint32_t { return cached ? s_key[r - r0] : rank[r]; };
 
-    const uint64_t a0 = t0 + (uint64_t)tid * kKeItems;
+    const uint32_t p0 = (uint32_t)tid * kKeItems;
     uint32_t v[kKeItems], kv[kKeItems];
-    if (vec4 && a0 + kKeItems <= t1) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(cols + a0);
+    if (vec4 && p0 + kKeItems <= len) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(cols + t0 + p0);
 #pragma unroll
         for (int q = 0; q < kKeItems / 4; q++) {
             const uint4 x = __ldg(p + q);
@@ -111,44 +159,37 @@ __global__ __launch_bounds__(kKeThreads) void k_rl_keep(
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < kKeItems; j++) v[j] = (a0 + j < t1) ? cols[a0 + j] : 0u;
+        for (int j = 0; j < kKeItems; j++) v[j] = (p0 + j < len) ? cols[t0 + p0 + j] : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < kKeItems; j++) kv[j] = (a0 + j < t1 && v[j] < n) ? __ldg(rank + v[j]) : 0u;
+    for (int j = 0; j < kKeItems; j++) kv[j] = (p0 + j < len && v[j] < n) ? __ldg(rank + v[j]) : 0u;
 
-    // the row of this thread's first arc: last r in [r0, u_next] with off[r] <= a0
-    uint32_t r_init = r0;
-    if (a0 < t1) {
-        uint32_t lo = r0, hi = u_next;
+    // tile row of this thread's first arc: last i with s_rel[i] <= p0 (s_rel[0] = 0)
+    uint32_t ri0 = 0;
+    if (p0 < len) {
+        uint32_t lo = 0, hi = nrows - 1;
         while (lo < hi) {
-            const uint32_t mid = lo + (hi - lo + 1) / 2;
-            if (row_start(mid) <= a0) lo = mid;
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (s_rel[mid] <= p0) lo = mid;
             else hi = mid - 1;
         }
-        r_init = lo;
+        ri0 = lo;
     }
-    const uint64_t rs_init = row_start(r_init);
 
-    // walk 1: keep mask
     uint32_t mask = 0;
-    if (a0 < t1) {
-        uint32_t r = r_init;
-        uint64_t re = row_start(r + 1);
-        uint32_t ku = row_key(r);
+    if (p0 < len) {
+        uint32_t ri = ri0, re = s_rel[ri + 1], ku = s_key[ri];
 #pragma unroll
         for (int j = 0; j < kKeItems; j++) {
-            const uint64_t a = a0 + j;
-            if (a < t1) {
-                while (re <= a && r + 1 < u_next) {
-                    r++;
-                    re = row_start(r + 1);
-                    ku = row_key(r);
+            const uint32_t p = p0 + j;
+            if (p < len) {
+                while (re <= p && ri + 1 < nrows) {
+                    ri++;
+                    re = s_rel[ri + 1];
+                    ku = s_key[ri];
                 }
-                if (v[j] >= n) {
-                    set_error(err, kDevBadInput);
-                    continue;
-                }
-                if (kv[j] > ku) mask |= 1u << j;
+                if (v[j] >= n) set_error(err, kDevBadInput);
+                else if (kv[j] > ku) mask |= 1u << j;
             }
         }
     }
@@ -158,69 +199,63 @@ __global__ __launch_bounds__(kKeThreads) void k_rl_keep(
     if (tid == 0) s_pref[kKeThreads] = total;
     __syncthreads();
 
-    // walk 2: every row piece that starts at one of this thread's arcs (its row's first arc, or
-    // the tile's first arc) reserves its place in the row with one atomic
-    if (a0 < t1) {
-        uint32_t r = r_init;
-        uint64_t rs = rs_init, re = row_start(r + 1);
-        uint32_t ku = row_key(r);
+    // each row piece reserves its place in its row with one atomic (thread per row)
+    for (uint32_t i = tid; i < nrows; i += kKeThreads) {
+        const uint32_t f = s_rel[i], e = s_rel[i + 1];
+        int32_t delta = kNoSlot;
+        if (e > f) {
+            const uint32_t pf = tile_prefix(s_pref, s_mask, f);
+            const uint32_t cnt = tile_prefix(s_pref, s_mask, e) - pf;
+            if (cnt) {
+                // the first and the last row may extend beyond the tile
+                uint64_t rowlen_true = e - f;
+                if (i == 0 || i == nrows - 1) {
+                    const uint64_t b = off[r0 + i], c = off[r0 + i + 1];
+                    rowlen_true = (b <= c && c <= arcs) ? c - b : 0;
+                }
+                const uint32_t key = s_key[i];
+                if (key < n) {
+                    const uint32_t base = atomicAdd(&rowlen[key], cnt);
+                    // a row cannot keep more arcs than it has (else the rank is not a
+                    // permutation); places stay far below 2^31
+                    if ((uint64_t)base + cnt <= rowlen_true && base < 0x40000000u)
+                        delta = (int32_t)base - (int32_t)pf;
+                    else
+                        set_error(err, kDevBadInput);
+                } else {
+                    set_error(err, kDevBadInput);
+                }
+            }
+        }
+        s_delta[i] = delta;
+    }
+    // kept ranks to shared memory in tile order, with their rows
+    if (mask) {
+        uint32_t ri = ri0, re = s_rel[ri + 1], q = s_pref[tid];
 #pragma unroll
         for (int j = 0; j < kKeItems; j++) {
-            const uint64_t a = a0 + j;
-            if (a < t1) {
-                while (re <= a && r + 1 < u_next) {
-                    r++;
-                    rs = re;
-                    re = row_start(r + 1);
-                    ku = row_key(r);
+            const uint32_t p = p0 + j;
+            if (p < len) {
+                while (re <= p && ri + 1 < nrows) {
+                    ri++;
+                    re = s_rel[ri + 1];
                 }
-                if (a == rs || a == t0) {
-                    const uint32_t f = (uint32_t)(a - t0);
-                    const uint32_t pf = tile_prefix(s_pref, s_mask, f);
-                    const uint32_t cnt = tile_prefix(s_pref, s_mask, (uint32_t)(min(re, t1) - t0)) - pf;
-                    int32_t delta = kNoSlot;
-                    if (cnt) {
-                        if (ku < n) {
-                            const uint32_t base = atomicAdd(&rowlen[ku], cnt);
-                            // a row cannot keep more arcs than it has (else the rank is not
-                            // a permutation); places stay far below 2^31
-                            if (rs <= re && re <= arcs && (uint64_t)base + cnt <= re - rs &&
-                                base < 0x40000000u)
-                                delta = (int32_t)base - (int32_t)pf;
-                            else
-                                set_error(err, kDevBadInput);
-                        } else {
-                            set_error(err, kDevBadInput);
-                        }
-                    }
-                    s_delta[f] = delta;
+                if (mask >> j & 1) {
+                    s_out[q] = kv[j];
+                    s_krow[q] = (uint16_t)ri;
+                    q++;
                 }
             }
         }
     }
     __syncthreads();
-
-    // walk 3: kept ranks to kept[off[u] + place]
-    if (mask) {
-        uint32_t r = r_init;
-        uint64_t rs = rs_init, re = row_start(r + 1);
-        uint32_t p = s_pref[tid];
-#pragma unroll
-        for (int j = 0; j < kKeItems; j++) {
-            const uint64_t a = a0 + j;
-            if (a < t1) {
-                while (re <= a && r + 1 < u_next) {
-                    r++;
-                    rs = re;
-                    re = row_start(r + 1);
-                }
-                if (mask >> j & 1) {
-                    const int32_t delta = s_delta[(uint32_t)(max(rs, t0) - t0)];
-                    if (delta != kNoSlot) kept[rs + (uint64_t)(int64_t)((int64_t)delta + p)] = kv[j];
-                    p++;
-                }
-            }
-        }
+    // consecutive kept ranks of a row piece go to consecutive places of the row
+    for (uint32_t q = tid; q < total; q += kKeThreads) {
+        const uint32_t ri = s_krow[q];
+        const int32_t delta = s_delta[ri];
+        if (delta == kNoSlot) continue;
+        const uint64_t rs = ri == 0 ? row0_start : t0 + s_rel[ri];
+        kept[rs + (uint64_t)(int64_t)((int64_t)delta + q)] = s_out[q];
     }
 }
 
