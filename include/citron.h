@@ -42,7 +42,8 @@ typedef enum {
     CITRON_E_CUDA = 3,        /* a CUDA runtime call failed (launch, copy, sync) */
     CITRON_E_OVERFLOW = 4,    /* the exact count does not fit in uint64 */
     CITRON_E_TIMEOUT = 5,     /* a bounded device wait gave up (the result is not valid) */
-    CITRON_E_UNSUPPORTED = 6  /* the input exceeds a documented size limit of this build */
+    CITRON_E_UNSUPPORTED = 6, /* the input exceeds a documented size limit of this build */
+    CITRON_E_BUDGET = 7       /* the count's time budget ran out before it finished (no result) */
 } citron_status;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -166,6 +167,7 @@ citron_status citron_list(uint32_t n, const uint64_t *d_dag_off, const uint32_t 
  */
 #define CITRON_COUNT_TIME_KERNELS 1u /* fill kernel_ms (events on `stream`) */
 #define CITRON_COUNT_WORK 2u         /* fill work_ops (a separately compiled, instrumented kernel) */
+#define CITRON_COUNT_BALANCE 4u      /* fill busy_ms (each bitmap-path block's start and end) */
 typedef struct {
     uint32_t small_max;      /* in: warp-register path for out-degree <= small_max, 0..32 (0: 32) */
     uint32_t bitmap_max;     /* in: shared-memory bitmap path up to this out-degree, <= 1024
@@ -181,6 +183,18 @@ typedef struct {
     uint64_t *d_per_root;    /* in: optional device array of n uint64, as in citron_count */
     uint64_t work_ops;       /* out: 32-bit AND+POPC word operations of the bitmap path */
     float kernel_ms[3];      /* out: device ms of the warp-register, bitmap, sorted-list kernels */
+    uint32_t split_min;      /* in: bitmap-path roots of at least this out-degree share their work
+                                with idle blocks (heavy-edge splitting, Sec. VII-C): their edge
+                                tasks -- and for k >= 6 the sub-tasks (u, a_t, b) of rows above
+                                128 members -- are taken from a global cursor, which blocks that
+                                find the root queue empty join after rebuilding the root's
+                                subgraph.  0: default (384); 1: never; else the threshold */
+    float busy_ms[2];        /* out (CITRON_COUNT_BALANCE): bitmap kernel's span from the first
+                                block start to the last block end, and its tail from the first
+                                block end to the last */
+    uint32_t budget_ms;      /* in: device time the count may take (0: no limit); when it runs
+                                out, the blocks stop taking work and the call returns
+                                CITRON_E_BUDGET */
 } citron_count_opts;
 
 citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,

@@ -24,6 +24,7 @@ STATUS = {
     4: "CITRON_E_OVERFLOW",
     5: "CITRON_E_TIMEOUT",
     6: "CITRON_E_UNSUPPORTED",
+    7: "CITRON_E_BUDGET",
 }
 
 # Every function the C ABI exports (checked against include/citron.h by the tests).
@@ -50,6 +51,7 @@ EXPORTS = (
 
 COUNT_TIME_KERNELS = 1
 COUNT_WORK = 2
+COUNT_BALANCE = 4
 
 
 class CountOpts(ctypes.Structure):
@@ -65,6 +67,9 @@ class CountOpts(ctypes.Structure):
         ("d_per_root", ctypes.c_void_p),
         ("work_ops", ctypes.c_uint64),
         ("kernel_ms", ctypes.c_float * 3),
+        ("split_min", ctypes.c_uint32),
+        ("busy_ms", ctypes.c_float * 2),
+        ("budget_ms", ctypes.c_uint32),
     ]
 
 
@@ -230,11 +235,15 @@ def citron_count(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, per
 def citron_count_ex(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, per_root=None,
                     stream=None, small_max: int = 0, bitmap_max: int = 0, warps_per_cta: int = 0,
                     time_kernels: bool = False, count_work: bool = False, compact_max: int = 0,
-                    max_blocks: int = 0):
-    """Returns (count, CountOpts) -- the options carry work_ops and kernel_ms on return."""
+                    max_blocks: int = 0, split_min: int = 0, balance: bool = False,
+                    budget_ms: int = 0):
+    """Returns (count, CountOpts) -- the options carry work_ops, kernel_ms and busy_ms on return."""
     o = CountOpts(small_max, bitmap_max, warps_per_cta,
-                  (COUNT_TIME_KERNELS if time_kernels else 0) | (COUNT_WORK if count_work else 0),
+                  (COUNT_TIME_KERNELS if time_kernels else 0) | (COUNT_WORK if count_work else 0)
+                  | (COUNT_BALANCE if balance else 0),
                   compact_max, max_blocks, _dptr(per_root).value, 0)
+    o.split_min = split_min
+    o.budget_ms = budget_ms
     out = ctypes.c_uint64(0)
     _check(lib().citron_count_ex(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg, ctypes.byref(o),
                                  ctypes.byref(out), _dptr(ws), _nbytes(ws), _stream(stream)),

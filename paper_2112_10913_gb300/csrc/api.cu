@@ -102,6 +102,7 @@ citron_status from_device(uint32_t code)
         case citron::kDevTooLong: return CITRON_E_UNSUPPORTED;
         case citron::kDevBadInput: return CITRON_E_INVALID;
         case citron::kDevScratch: return CITRON_E_WORKSPACE;
+        case citron::kDevBudget: return CITRON_E_BUDGET;
         default: return CITRON_E_CUDA;
     }
 }
@@ -141,6 +142,7 @@ const char *citron_status_str(citron_status s)
         case CITRON_E_OVERFLOW: return "count exceeds uint64";
         case CITRON_E_TIMEOUT: return "bounded device wait gave up";
         case CITRON_E_UNSUPPORTED: return "input exceeds a size limit of this build";
+        case CITRON_E_BUDGET: return "time budget ran out before the count finished";
     }
     return "unknown status";
 }
@@ -156,6 +158,7 @@ static bool plan_from_opts(const citron_count_opts *opts, CountPlan &plan)
     if (opts->bitmap_max) plan.bitmap_max = opts->bitmap_max;
     if (opts->warps_per_cta) plan.warps_per_cta = opts->warps_per_cta;
     if (opts->compact_max) plan.compact_max = opts->compact_max == 1 ? 0 : opts->compact_max;
+    if (opts->split_min) plan.split_min = opts->split_min == 1 ? 0xffffffffu : opts->split_min;
     plan.max_blocks = opts->max_blocks;
     if (plan.bitmap_max < plan.small_max) plan.bitmap_max = plan.small_max;
     return true;
@@ -261,8 +264,11 @@ citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint3
     run.sink.per_root = (unsigned long long *)opts->d_per_root;
     run.time_kernels = (opts->flags & CITRON_COUNT_TIME_KERNELS) != 0;
     run.count_work = (opts->flags & CITRON_COUNT_WORK) != 0;
+    run.balance = (opts->flags & CITRON_COUNT_BALANCE) != 0;
+    run.budget_ns = (unsigned long long)opts->budget_ms * 1000000ull;
     opts->work_ops = 0;
     opts->kernel_ms[0] = opts->kernel_ms[1] = opts->kernel_ms[2] = 0.f;
+    opts->busy_ms[0] = opts->busy_ms[1] = 0.f;
     cudaStream_t s = (cudaStream_t)stream;
     if (!ws_ok(ws, ws_bytes, kHeader)) return CITRON_E_WORKSPACE;
     if (k <= 2) {
@@ -290,6 +296,8 @@ citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint3
     if (st == CITRON_OK) *h_count = result;
     opts->work_ops = run.work;
     for (int i = 0; i < 3; i++) opts->kernel_ms[i] = run.kernel_ms[i];
+    opts->busy_ms[0] = run.busy_ms[0];
+    opts->busy_ms[1] = run.busy_ms[1];
     return st;
 }
 

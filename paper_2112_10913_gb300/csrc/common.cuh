@@ -22,6 +22,7 @@ enum DevErr : uint32_t {
     kDevTooLong = 3,      // a row exceeded a compiled capacity
     kDevBadInput = 4,     // input violated the CSR contract where the kernel checks it
     kDevScratch = 5,      // workspace sized for a smaller max out-degree than the input has
+    kDevBudget = 6,       // the count's time budget ran out
 };
 
 __device__ __forceinline__ void set_error(uint32_t *err, uint32_t code)
@@ -39,6 +40,35 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 struct WaitCfg {
     uint32_t spin_limit = kSpinLimit;
     uint32_t stall_tile = 0xffffffffu;
+};
+
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Time budget of one count shared by all of its launches: clock0 holds the global time of the
+// first check (0 before it); a block asks before it takes more work.
+struct Budget {
+    unsigned long long *clock0 = nullptr;
+    unsigned long long ns = 0;  // 0: no limit
+
+    __device__ __forceinline__ bool over(uint32_t *err) const
+    {
+        if (!ns) return false;
+        const unsigned long long now = global_ns();
+        unsigned long long t0 = *(volatile unsigned long long *)clock0;
+        if (t0 == 0) {
+            t0 = atomicCAS(clock0, 0ull, now);
+            if (t0 == 0) t0 = now;
+        }
+        if (now - t0 <= ns) return false;
+        set_error(err, kDevBudget);
+        return true;
+    }
 };
 
 // Exact uint64 accumulation into a global counter; flags a wrap past 2^64 - 1.
@@ -186,7 +216,33 @@ struct RootSink {
             else set_error(err, kDevBadInput);
         }
     }
+    // A root counted by several blocks (a split heavy root): each adds its part.
+    __device__ __forceinline__ void add(uint32_t u, unsigned long long r, uint32_t *err) const
+    {
+        if (per_root) add_checked(&per_root[u], r, err);
+        if (group_counts) {
+            const uint32_t g = group_of_row[u];
+            if (g < ngroups) add_checked(&group_counts[g], r, err);
+            else set_error(err, kDevBadInput);
+        }
+    }
     __device__ __forceinline__ bool wants_root_total() const { return per_root || group_counts; }
+};
+
+// A heavy root whose units (edge tasks, or edge sub-tasks (u, a_t, b)) any block may take: the
+// block that took the root from the queue publishes it here; blocks that find the root queue
+// empty rebuild its local subgraph and take units from the same cursor.
+struct HeavySlot {
+    uint32_t u;       // the root
+    uint32_t units;   // size of its unit space
+    uint32_t cursor;  // next unit to take (may run past `units`)
+    uint32_t ready;   // 1 once u and units are published
+};
+
+struct HelpTable {
+    HeavySlot *slots = nullptr;
+    uint32_t cap = 0;
+    uint32_t *nslots = nullptr;  // slots taken so far (may run past cap: those roots get no help)
 };
 
 // Which roots a counting pass takes, besides the out-degree prune: with group_of_row set, only
@@ -219,6 +275,8 @@ struct CountPlan {
     uint32_t warps_per_cta = 32;   // warps per block of the bitmap path (fewer if shared memory is short)
     uint32_t compact_max = 128;    // candidate sets up to this size are re-encoded compactly (0: never)
     uint32_t max_blocks = 0;       // cap on the blocks of each counting launch (0: no cap)
+    uint32_t split_min = 384;      // bitmap-path roots of at least this out-degree share their units
+                                   // with idle blocks (0xffffffff: never)
 };
 
 // Options and outputs of one counting call.
@@ -228,8 +286,12 @@ struct CountRun {
     citron::RootFilter filter;                               // roots of this pass
     bool count_work = false;                 // instrumented launch: count word operations
     bool time_kernels = false;               // record device time of the counting kernels
+    bool balance = false;                    // record when each bitmap-path block starts and ends
+    unsigned long long budget_ns = 0;        // device time the count may take (0: no limit)
     unsigned long long work = 0;             // out: word operations (AND + POPC of 32-bit words)
     float kernel_ms[3] = {0, 0, 0};          // out: warp-register, bitmap, sorted-list kernels
+    float busy_ms[2] = {0, 0};               // out: bitmap kernel's span (first start to last end)
+                                             // and tail (first block end to last block end)
 };
 
 // Number of kernels this library has launched (all devices, all threads).

@@ -36,13 +36,6 @@ struct CoreState {
     unsigned int level;
 };
 
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ __forceinline__ uint32_t load_relaxed(unsigned int *p)
 {
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> r(*p);

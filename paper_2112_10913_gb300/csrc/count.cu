@@ -180,13 +180,15 @@ size_t count_ws_bytes(uint32_t n, uint32_t max_outdeg, int num_sms)
 {
     Sizer s;
     s.take<CountStats>(1);
-    s.take<unsigned long long>(2);
+    s.take<unsigned long long>(4);
     s.take<uint32_t>(8);                      // queue counters
     s.take<uint32_t>((size_t)n + 1);          // small list
     s.take<uint32_t>((size_t)n + 1);          // mid list
     s.take<uint32_t>((size_t)n + 1);          // big list
     s.take<uint32_t>(kBitmapCap + 2);         // mid histogram
     s.take<uint32_t>(kBitmapCap + 2);         // mid cursors
+    s.take<HeavySlot>(kHelpSlots);            // help table of heavy roots
+    s.take<unsigned long long>(2 * (size_t)num_sms * kMidBlocksPerSmCap);  // block start/end
     // sorted-list scratch: one (k-3)-level stack per warp, sized for the largest root, so that
     // every root can take the list path (tuned thresholds send any root there)
     const uint32_t list_warps = (uint32_t)num_sms * kListWarps;
@@ -201,13 +203,20 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
                       unsigned long long *h_result)
 {
     CountStats *st = c.take<CountStats>(1);
-    unsigned long long *result = c.take<unsigned long long>(2);
+    unsigned long long *result = c.take<unsigned long long>(4);  // total, work, budget clock
     uint32_t *next = c.take<uint32_t>(8);
     uint32_t *small_list = c.take<uint32_t>((size_t)n + 1);
     uint32_t *mid_list = c.take<uint32_t>((size_t)n + 1);
     uint32_t *big_list = c.take<uint32_t>((size_t)n + 1);
     uint32_t *hist = c.take<uint32_t>(kBitmapCap + 2);
     uint32_t *cursor = c.take<uint32_t>(kBitmapCap + 2);
+    MidAux aux;
+    aux.help.slots = c.take<HeavySlot>(kHelpSlots);
+    aux.help.cap = kHelpSlots;
+    aux.help.nslots = next + 2;
+    aux.block_ns = c.take<unsigned long long>(2 * (size_t)num_sms * kMidBlocksPerSmCap);
+    aux.budget.clock0 = result + 2;
+    aux.budget.ns = run.budget_ns;
     if (!c.ok) return cudaErrorMemoryAllocation;
     // the rest of the workspace is list-path scratch
     uint32_t *list_scratch = (uint32_t *)(c.base + c.used);
@@ -217,10 +226,11 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
 
     cudaError_t e;
     if ((e = cudaMemsetAsync(st, 0, sizeof(CountStats), s))) return e;
-    if ((e = cudaMemsetAsync(result, 0, 2 * sizeof(unsigned long long), s))) return e;
+    if ((e = cudaMemsetAsync(result, 0, 4 * sizeof(unsigned long long), s))) return e;
     if ((e = seed_totals(result, 1, s))) return e;
     if ((e = cudaMemsetAsync(next, 0, 8 * sizeof(uint32_t), s))) return e;
     if ((e = cudaMemsetAsync(hist, 0, (kBitmapCap + 2) * sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(aux.help.slots, 0, kHelpSlots * sizeof(HeavySlot), s))) return e;
     const uint32_t need = k - 1;
     const uint32_t blocks = (n + 255) / 256;
     if (n) {
@@ -238,7 +248,8 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
 #define CITRON_CASE(KK)                                                                           \
     case KK:                                                                                      \
         e = launch_count_##KK(run, dag_off, dag_cols, hs, st, small_list, mid_list, big_list,     \
-                               next, list_scratch, list_words, result, work, err, s, num_sms);    \
+                               next, list_scratch, list_words, result, work, aux, err, s,         \
+                               num_sms);                                                          \
         break;
     switch (k) {
         CITRON_CASE(3)
@@ -271,13 +282,20 @@ cudaError_t run_count_async(uint32_t n, const uint64_t *dag_off, const uint32_t 
                             cudaStream_t s, int num_sms)
 {
     CountStats *st = c.take<CountStats>(1);
-    unsigned long long *result = c.take<unsigned long long>(2);
+    unsigned long long *result = c.take<unsigned long long>(4);  // total, work, budget clock
     uint32_t *next = c.take<uint32_t>(8);
     uint32_t *small_list = c.take<uint32_t>((size_t)n + 1);
     uint32_t *mid_list = c.take<uint32_t>((size_t)n + 1);
     uint32_t *big_list = c.take<uint32_t>((size_t)n + 1);
     uint32_t *hist = c.take<uint32_t>(kBitmapCap + 2);
     uint32_t *cursor = c.take<uint32_t>(kBitmapCap + 2);
+    MidAux aux;
+    aux.help.slots = c.take<HeavySlot>(kHelpSlots);
+    aux.help.cap = kHelpSlots;
+    aux.help.nslots = next + 2;
+    aux.block_ns = c.take<unsigned long long>(2 * (size_t)num_sms * kMidBlocksPerSmCap);
+    aux.budget.clock0 = result + 2;
+    aux.budget.ns = run.budget_ns;
     if (!c.ok) return cudaErrorMemoryAllocation;
     uint32_t *list_scratch = (uint32_t *)(c.base + c.used);
     const size_t list_words = c.cap > c.used ? (c.cap - c.used) / sizeof(uint32_t) : 0;
@@ -285,9 +303,10 @@ cudaError_t run_count_async(uint32_t n, const uint64_t *dag_off, const uint32_t 
     const CountPlan &plan = run.plan;
     cudaError_t e;
     if ((e = cudaMemsetAsync(st, 0, sizeof(CountStats), s))) return e;
-    if ((e = cudaMemsetAsync(result, 0, 2 * sizeof(unsigned long long), s))) return e;
+    if ((e = cudaMemsetAsync(result, 0, 4 * sizeof(unsigned long long), s))) return e;
     if ((e = cudaMemsetAsync(next, 0, 8 * sizeof(uint32_t), s))) return e;
     if ((e = cudaMemsetAsync(hist, 0, (kBitmapCap + 2) * sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(aux.help.slots, 0, kHelpSlots * sizeof(HeavySlot), s))) return e;
     if (n == 0 || max_outdeg < k - 1) return cudaSuccess;
     const uint32_t need = k - 1;
     const uint32_t blocks = (n + 255) / 256;
@@ -307,7 +326,8 @@ cudaError_t run_count_async(uint32_t n, const uint64_t *dag_off, const uint32_t 
 #define CITRON_CASE(KK)                                                                           \
     case KK:                                                                                      \
         e = launch_count_##KK(run, dag_off, dag_cols, hs, st, small_list, mid_list, big_list,     \
-                              next, list_scratch, list_words, result, work, err, s, num_sms);    \
+                              next, list_scratch, list_words, result, work, aux, err, s,         \
+                              num_sms);                                                          \
         break;
     switch (k) {
         CITRON_CASE(3)

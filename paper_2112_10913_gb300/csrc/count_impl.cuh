@@ -63,7 +63,7 @@ template <int K>
 __global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
     const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
     const uint32_t *__restrict__ list, const CountStats *st, unsigned long long *result,
-    RootSink sink, uint32_t *err)
+    RootSink sink, Budget budget, uint32_t *err)
 {
     __shared__ uint32_t sL[kSmallWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -71,6 +71,9 @@ __global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
     const uint32_t gw = blockIdx.x * kSmallWarps + w, nwarps = gridDim.x * kSmallWarps;
     unsigned long long total = 0;
     for (uint32_t idx = gw; idx < nlist; idx += nwarps) {
+        int stop = 0;
+        if (lane == 0) stop = budget.over(err);
+        if (__shfl_sync(kFull, stop, 0)) break;
         const uint32_t u = list[idx];
         const uint64_t base = dag_off[u];
         const uint32_t D = (uint32_t)(dag_off[u + 1] - base);
@@ -750,22 +753,90 @@ __host__ __device__ __forceinline__ uint32_t warp_scratch_words(uint32_t dcap, u
 }
 
 constexpr int kMidMaxWarps = 32;
+constexpr uint32_t kSplitMembers = 128;  // k >= 6: rows above this many members split per member
+constexpr uint32_t kNoHelpSlot = 0xffffffffu;
+constexpr uint32_t kHelpSlots = 8192;    // heavy roots that can take help, per launch
 
+// Position of the r-th (from 0) set bit of x (r < popc(x)).
+__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t r)
+{
+    uint32_t pos = 0;
+#pragma unroll
+    for (int width = 16; width > 0; width >>= 1) {
+        const uint32_t low = __popc(x & ((1u << width) - 1u));
+        if (r >= low) {
+            r -= low;
+            x >>= width;
+            pos += width;
+        }
+    }
+    return pos;
+}
+
+// Warp 0: the published heavy root with the most units left (kNoHelpSlot when none has any).
+__device__ __forceinline__ uint32_t pick_help_slot(const HelpTable &ht, int lane)
+{
+    const uint32_t ns = min(*(volatile uint32_t *)ht.nslots, ht.cap);
+    uint32_t best = kNoHelpSlot, best_rem = 0;
+    for (uint32_t s0 = 0; s0 < ns; s0 += 32) {
+        const uint32_t sl = s0 + lane;
+        uint32_t rem = 0;
+        if (sl < ns) {
+            cuda::atomic_ref<uint32_t, cuda::thread_scope_device> ready(ht.slots[sl].ready);
+            if (ready.load(cuda::memory_order_acquire)) {
+                const uint32_t units = ht.slots[sl].units;
+                const uint32_t cur = *(volatile uint32_t *)&ht.slots[sl].cursor;
+                rem = cur < units ? units - cur : 0u;
+            }
+        }
+        uint32_t bsl = sl;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint32_t r2 = __shfl_xor_sync(kFull, rem, o), s2 = __shfl_xor_sync(kFull, bsl, o);
+            if (r2 > rem || (r2 == rem && s2 < bsl)) {
+                rem = r2;
+                bsl = s2;
+            }
+        }
+        if (rem > best_rem) {
+            best_rem = rem;
+            best = bsl;
+        }
+    }
+    return best;
+}
+
+// Bitmap path (small_max < D <= dcap): one block per root, roots taken largest-D first from the
+// queue.  The block builds the root's local subgraph as D x D bitmap rows in shared memory
+// (row i = V(g_u) ∩ N+(a_i), Algorithm GenSub-CITRON by sorted-list intersection) and its warps
+// count the (K-2)-cliques of every row.
+//   D < split_min: the rows (edge tasks (u, a_t)) are taken from a counter in shared memory.
+//   D >= split_min (heavy roots, K >= 4): the root's work is a space of units -- one per edge task,
+//       or, for K >= 6, one per member b of a row of more than 128 members (the edge sub-task
+//       (u, a_t, b): the (K-3)-cliques of row_t ∧ row_b) -- taken from a cursor in a global
+//       table.  Blocks that find the root queue empty pick the published heavy root with the
+//       most units left, rebuild its rows and take units from the same cursor (work stealing
+//       across blocks); every block adds its own part of the root's count.
+// block_ns (optional): each block's start and end on the global timer.
 template <int K, bool WORK>
 __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
     const uint32_t *__restrict__ list, const CountStats *st, uint32_t *next, uint32_t dcap,
-    uint32_t compact_max, unsigned long long *result, RootSink sink,
-    unsigned long long *work_out, uint32_t *err)
+    uint32_t compact_max, uint32_t split_min, HelpTable ht, unsigned long long *result,
+    RootSink sink, unsigned long long *work_out, unsigned long long *block_ns, Budget budget,
+    uint32_t *err)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t rs_cap = (dcap / 32) | 1;
     uint32_t *sL = smem;
     uint32_t *rows = smem + dcap;
-    __shared__ uint32_t s_idx, s_task, s_tri;
+    __shared__ uint32_t s_idx, s_task, s_tri, s_slot, s_u, s_units;
     __shared__ unsigned long long s_acc[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t *wscr = rows + (size_t)dcap * rs_cap + (size_t)w * warp_scratch_words(dcap, compact_max);
+    const uint32_t wsw = warp_scratch_words(dcap, compact_max);
+    uint32_t *wscr = rows + (size_t)dcap * rs_cap + (size_t)w * wsw;
+    // unit prefix of a heavy root's rows: it reuses sL, which is dead once the rows are built
+    uint32_t *s_upre = sL;
     WarpCtx x;
     x.rows = rows;
     x.elem = reinterpret_cast<uint16_t *>(wscr);
@@ -776,19 +847,40 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     x.compact_max = compact_max;
     x.compact3_max = compact_max ? 192u : 0u;
     const uint32_t nlist = st->n_mid;
+    if (block_ns && threadIdx.x == 0) block_ns[2 * blockIdx.x] = global_ns();
     unsigned long long block_total = 0;  // meaningful in thread 0
+    bool queue_empty = false;
     for (;;) {
         if (threadIdx.x == 0) {
-            s_idx = atomicAdd(next, 1u);
+            s_idx = queue_empty || budget.over(err) ? 0xfffffffeu : atomicAdd(next, 1u);
             s_task = 0;
             s_tri = 1;
+            s_slot = kNoHelpSlot;
         }
         __syncthreads();
         const uint32_t idx = s_idx;
-        if (idx >= nlist) break;
-        const uint32_t u = list[idx];
+        const bool owner = idx < nlist;
+        if (!owner) {
+            queue_empty = true;
+            if (K < 4 || ht.slots == nullptr || idx == 0xfffffffeu) break;
+            if (w == 0) {
+                const uint32_t sl = pick_help_slot(ht, lane);
+                if (lane == 0) {
+                    s_slot = sl;
+                    if (sl != kNoHelpSlot) s_u = ht.slots[sl].u;
+                }
+            }
+            __syncthreads();
+            if (s_slot == kNoHelpSlot) break;
+        }
+        const uint32_t u = owner ? list[idx] : s_u;
         const uint64_t base = dag_off[u];
         const uint32_t D = (uint32_t)(dag_off[u + 1] - base);
+        if (D > dcap || D == 0) {  // a root is never larger than the launch's capacity
+            if (threadIdx.x == 0) set_error(err, kDevBadInput);
+            break;
+        }
+        const bool heavy = K >= 4 && (!owner || D >= split_min);
         const uint32_t W = (D + 31) >> 5, RS = W | 1;
         for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) sL[i] = dag_cols[base + i];
         if (K > 3)
@@ -797,7 +889,8 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
         const uint32_t lmax = sL[D - 1];
         unsigned long long acc = 0, work = 0;
         // Build the local subgraph: row i = V(g_u) ∩ N+(a_i) (CITRON's GenSubgraph).  Each step
-        // loads 64 entries of N+(a_i) (two per lane) so that two loads are in flight.
+        // loads 64 entries of N+(a_i) (two per lane) so that two loads are in flight.  (A block
+        // helping with a heavy root rebuilds the same rows; its triangles are not counted here.)
         bool tri = true;
         for (uint32_t i = w; i < D; i += nw) {
             const uint32_t a = sL[i];
@@ -829,15 +922,86 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
             x.RS = RS;
             x.W = W;
             x.tri = s_tri != 0;
-            // Edge tasks (u, a_t): count (K-2)-cliques in row t.
+            // Units: edge tasks (u, a_t) -- count (K-2)-cliques in row t -- one per row for a light
+            // root; for a heavy root the unit space of its rows (prefix in s_upre), shared with
+            // helping blocks through its slot.
+            uint32_t U = D;
+            if (heavy) {
+                for (uint32_t t = w; t < D; t += nw) {
+                    const uint32_t c = lane < W ? rows[t * RS + lane] : 0u;
+                    const uint32_t m = __reduce_add_sync(kFull, __popc(c));
+                    if (lane == 0)
+                        s_upre[t] = m < (uint32_t)(K - 2) ? 0u : ((K >= 6 && m > kSplitMembers) ? m : 1u);
+                }
+                __syncthreads();
+                if (w == 0) {
+                    uint32_t run = 0;
+                    for (uint32_t t0 = 0; t0 < D; t0 += 32) {
+                        const uint32_t v = t0 + lane < D ? s_upre[t0 + lane] : 0u;
+                        const uint32_t inc = warp_incl_scan(v);
+                        if (t0 + lane < D) s_upre[t0 + lane] = run + inc - v;
+                        run += __shfl_sync(kFull, inc, 31);
+                    }
+                    if (lane == 0) s_units = run;
+                }
+                __syncthreads();
+                U = s_units;
+                if (threadIdx.x == 0) {
+                    if (owner && ht.slots) {
+                        const uint32_t sl = atomicAdd(ht.nslots, 1u);
+                        if (sl < ht.cap) {
+                            ht.slots[sl].u = u;
+                            ht.slots[sl].units = U;
+                            ht.slots[sl].cursor = 0;
+                            cuda::atomic_ref<uint32_t, cuda::thread_scope_device> ready(ht.slots[sl].ready);
+                            ready.store(1u, cuda::memory_order_release);
+                            s_slot = sl;
+                        }
+                    } else if (!owner && ht.slots[s_slot].units != U) {
+                        set_error(err, kDevBadInput);  // the rebuilt root differs from the published one
+                        s_task = U;                    // take nothing
+                    }
+                }
+                __syncthreads();
+            }
+            uint32_t *cursor = (s_slot != kNoHelpSlot && (owner || s_task == 0)) ? &ht.slots[s_slot].cursor
+                                                                                   : &s_task;
             for (;;) {
-                uint32_t t = 0;
-                if (lane == 0) t = atomicAdd(&s_task, 1u);
-                t = __shfl_sync(kFull, t, 0);
-                if (t >= D) break;
+                uint32_t i = 0;
+                if (lane == 0) i = heavy && budget.over(err) ? U : atomicAdd(cursor, 1u);
+                i = __shfl_sync(kFull, i, 0);
+                if (i >= U) break;
+                uint32_t t = i, j = 0;
+                bool whole = true;
+                if (heavy) {
+                    // the row of unit i: the last t with s_upre[t] <= i
+                    uint32_t lo = 0, hi = D - 1;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (s_upre[mid] <= i) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    t = lo;
+                    j = i - s_upre[t];
+                    whole = (t + 1 < D ? s_upre[t + 1] : U) - s_upre[t] == 1u;
+                }
                 const uint32_t c = lane < W ? rows[t * RS + lane] : 0u;
-                const uint32_t cnt = __reduce_add_sync(kFull, __popc(c));
-                if (cnt >= K - 2) warp_dfs<K - 2, WORK>(x, c, lane, acc, work);
+                if (whole) {
+                    const uint32_t cnt = __reduce_add_sync(kFull, __popc(c));
+                    if (cnt >= K - 2) warp_dfs<K - 2, WORK>(x, c, lane, acc, work);
+                } else if constexpr (K >= 6) {
+                    // the j-th member b of row t: the sub-task (u, a_t, b)
+                    const uint32_t pc = __popc(c);
+                    const uint32_t incl = warp_incl_scan(pc);
+                    const int wl = __ffs(__ballot_sync(kFull, incl > j)) - 1;
+                    const uint32_t before = __shfl_sync(kFull, incl - pc, wl);
+                    const uint32_t word = __shfl_sync(kFull, c, wl);
+                    const uint32_t b = (uint32_t)wl * 32 + select_bit(word, j - before);
+                    const uint32_t c2 = lane < W ? (c & rows[b * RS + lane]) : 0u;
+                    if (WORK && lane < (int)W) work += 1;
+                    const uint32_t cnt = __reduce_add_sync(kFull, __popc(c2));
+                    if (cnt >= K - 3) warp_dfs<K - 3, WORK>(x, c2, lane, acc, work);
+                }
             }
         }
         if (WORK) {
@@ -856,14 +1020,20 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
                 r = s2;
             }
             if (wrapped) set_error(err, kDevOverflow);
-            if (sink.wants_root_total()) sink.put(u, r, err);
+            if (sink.wants_root_total()) {
+                if (heavy) sink.add(u, r, err);
+                else sink.put(u, r, err);
+            }
             const unsigned long long s2 = block_total + r;
             if (s2 < block_total) set_error(err, kDevOverflow);
             block_total = s2;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) add_checked(result, block_total, err);
+    if (threadIdx.x == 0) {
+        add_checked(result, block_total, err);
+        if (block_ns) block_ns[2 * blockIdx.x + 1] = global_ns();
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -918,7 +1088,7 @@ template <int K>
 __global__ __launch_bounds__(kListWarps * 32) void k_count_list(
     const uint64_t *__restrict__ dag_off, const uint32_t *__restrict__ dag_cols,
     const uint32_t *__restrict__ list, const CountStats *st, uint32_t *next, uint32_t *scratch,
-    uint32_t stride, unsigned long long *result, RootSink sink, uint32_t *err)
+    uint32_t stride, unsigned long long *result, RootSink sink, Budget budget, uint32_t *err)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = blockIdx.x * kListWarps + (threadIdx.x >> 5);
@@ -927,7 +1097,7 @@ __global__ __launch_bounds__(kListWarps * 32) void k_count_list(
     unsigned long long total = 0;
     for (;;) {
         uint32_t idx = 0;
-        if (lane == 0) idx = atomicAdd(next, 1u);
+        if (lane == 0) idx = budget.over(err) ? nlist : atomicAdd(next, 1u);
         idx = __shfl_sync(kFull, idx, 0);
         if (idx >= nlist) break;
         const uint32_t u = list[idx];
@@ -954,6 +1124,15 @@ __global__ __launch_bounds__(kListWarps * 32) void k_count_list(
 namespace citron_host {
 using namespace citron;
 
+// Global-memory helpers of the bitmap kernel: the help table of heavy roots and the per-block
+// start/end times (2 words per block, kMidBlocksPerSmCap blocks per SM at most).
+constexpr uint32_t kMidBlocksPerSmCap = 8;
+struct MidAux {
+    HelpTable help;
+    unsigned long long *block_ns = nullptr;
+    Budget budget;  // the count's time budget (all of its launches)
+};
+
 struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
     bool on;
@@ -979,11 +1158,13 @@ struct Timer {
 
 template <int K, bool WORK>
 static cudaError_t launch_mid(uint32_t grid_cap, uint32_t block_cap, uint32_t dcap,
-                              uint32_t compact_max, uint32_t warps, size_t smem,
-                              const uint64_t *dag_off, const uint32_t *dag_cols,
-                              const uint32_t *mid_list, const CountStats *st, uint32_t *next,
-                              unsigned long long *result, RootSink sink,
-                              unsigned long long *work, uint32_t *err, cudaStream_t s, int num_sms)
+                              uint32_t compact_max, uint32_t split_min, const HelpTable &ht,
+                              uint32_t warps, size_t smem, const uint64_t *dag_off,
+                              const uint32_t *dag_cols, const uint32_t *mid_list,
+                              const CountStats *st, uint32_t *next, unsigned long long *result,
+                              RootSink sink, unsigned long long *work, unsigned long long *block_ns,
+                              Budget budget, uint32_t *grid_out, uint32_t *err, cudaStream_t s,
+                              int num_sms)
 {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_count_mid<K, WORK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -997,8 +1178,11 @@ static cudaError_t launch_mid(uint32_t grid_cap, uint32_t block_cap, uint32_t dc
     uint32_t grid = (uint32_t)(num_sms * per_sm);
     if (grid > grid_cap) grid = grid_cap;
     if (block_cap && grid > block_cap) grid = block_cap;
+    if (grid > (uint32_t)num_sms * kMidBlocksPerSmCap) grid = (uint32_t)num_sms * kMidBlocksPerSmCap;
+    *grid_out = grid;
     k_count_mid<K, WORK><<<grid, warps * 32, smem, s>>>(dag_off, dag_cols, mid_list, st, next, dcap,
-                                                        compact_max, result, sink, work, err);
+                                                        compact_max, split_min, ht, result, sink,
+                                                        work, block_ns, budget, err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -1009,8 +1193,8 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
                                   const uint32_t *small_list, const uint32_t *mid_list,
                                   const uint32_t *big_list, uint32_t *next, uint32_t *list_scratch,
                                   size_t list_scratch_words, unsigned long long *result,
-                                  unsigned long long *work, uint32_t *err, cudaStream_t s,
-                                  int num_sms)
+                                  unsigned long long *work, const MidAux &aux, uint32_t *err,
+                                  cudaStream_t s, int num_sms)
 {
     cudaError_t e = cudaSuccess;
     const CountPlan &plan = run.plan;
@@ -1030,17 +1214,39 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         uint32_t warps = plan.warps_per_cta > (uint32_t)kMidMaxWarps ? kMidMaxWarps : plan.warps_per_cta;
         while (warps > 1 && smem_for(warps) > (size_t)smem_cap) warps--;
         Timer t(run.time_kernels, s);
+        unsigned long long *block_ns = run.balance ? aux.block_ns : nullptr;
+        uint32_t grid = 0;
         if (run.count_work)
-            e = launch_mid<K, true>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
-                                    mid_list, st, next + 0, result, run.sink, work, err, s,
+            e = launch_mid<K, true>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, plan.split_min,
+                                    aux.help, warps, smem_for(warps), dag_off, dag_cols, mid_list, st,
+                                    next + 0, result, run.sink, work, block_ns, aux.budget, &grid, err, s,
                                     num_sms);
         else
-            e = launch_mid<K, false>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, warps, smem_for(warps), dag_off, dag_cols,
-                                     mid_list, st, next + 0, result, run.sink, work, err, s,
-                                     num_sms);
+            e = launch_mid<K, false>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, plan.split_min,
+                                     aux.help, warps, smem_for(warps), dag_off, dag_cols, mid_list, st,
+                                     next + 0, result, run.sink, work, block_ns, aux.budget, &grid, err, s,
+                                    num_sms);
         if (e) return e;
         t.stop();
         run.kernel_ms[1] = t.ms();
+        if (block_ns && grid) {
+            // span = first block start .. last block end; tail = first block end .. last block end
+            unsigned long long h[2 * kMidBlocksPerSmCap * 256];
+            const size_t cnt = 2 * (size_t)grid;
+            if (cnt <= sizeof(h) / sizeof(h[0])) {
+                e = cudaMemcpyAsync(h, block_ns, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+                if (!e) e = cudaStreamSynchronize(s);
+                if (e) return e;
+                unsigned long long s0 = ~0ull, e0 = ~0ull, e1 = 0;
+                for (uint32_t b = 0; b < grid; b++) {
+                    s0 = h[2 * b] < s0 ? h[2 * b] : s0;
+                    e0 = h[2 * b + 1] < e0 ? h[2 * b + 1] : e0;
+                    e1 = h[2 * b + 1] > e1 ? h[2 * b + 1] : e1;
+                }
+                run.busy_ms[0] = (float)((e1 - s0) * 1e-6);
+                run.busy_ms[1] = (float)((e1 - e0) * 1e-6);
+            }
+        }
     }
     if (hs.n_small) {
         uint32_t grid = (hs.n_small + kSmallWarps - 1) / kSmallWarps;
@@ -1049,7 +1255,7 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         if (grid > cap) grid = cap;
         Timer t(run.time_kernels, s);
         k_count_small<K><<<grid, kSmallWarps * 32, 0, s>>>(dag_off, dag_cols, small_list, st, result,
-                                                           run.sink, err);
+                                                           run.sink, aux.budget, err);
         note_launches(1);
         if ((e = cudaGetLastError())) return e;
         t.stop();
@@ -1067,7 +1273,7 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         Timer t(run.time_kernels, s);
         k_count_list<K><<<grid, kListWarps * 32, 0, s>>>(dag_off, dag_cols, big_list, st, next + 1,
                                                          list_scratch, hs.max_big, result,
-                                                         run.sink, err);
+                                                         run.sink, aux.budget, err);
         note_launches(1);
         if ((e = cudaGetLastError())) return e;
         t.stop();
@@ -1083,14 +1289,14 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
                                   const uint32_t *small_list, const uint32_t *mid_list,             \
                                   const uint32_t *big_list, uint32_t *next, uint32_t *list_scratch, \
                                   size_t list_scratch_words, unsigned long long *result,            \
-                                  unsigned long long *work, uint32_t *err, cudaStream_t s,          \
-                                  int num_sms)
+                                  unsigned long long *work, const MidAux &aux, uint32_t *err,       \
+                                  cudaStream_t s, int num_sms)
 #define CITRON_LAUNCH_K_DEF(KK)                                                                      \
     CITRON_LAUNCH_K_DECL(KK)                                                                         \
     {                                                                                                \
         return launch_count_k<KK>(run, dag_off, dag_cols, hs, st, small_list, mid_list, big_list,   \
-                                  next, list_scratch, list_scratch_words, result, work, err, s,     \
-                                  num_sms);                                                         \
+                                  next, list_scratch, list_scratch_words, result, work, aux, err,   \
+                                  s, num_sms);                                                      \
     }
 CITRON_LAUNCH_K_DECL(3);
 CITRON_LAUNCH_K_DECL(4);

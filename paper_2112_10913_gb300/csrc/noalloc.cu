@@ -114,6 +114,7 @@ extern "C" citron_status citron_count_noalloc(uint32_t n, const uint64_t *d_dag_
         case citron::kDevTooLong: return CITRON_E_UNSUPPORTED;
         case citron::kDevBadInput: return CITRON_E_INVALID;
         case citron::kDevScratch: return CITRON_E_WORKSPACE;
+        case citron::kDevBudget: return CITRON_E_BUDGET;
         default: return CITRON_E_CUDA;
     }
 }

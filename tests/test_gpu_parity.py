@@ -89,6 +89,9 @@ PATHS = {
     "small+list": dict(small_max=32, bitmap_max=32),
     "list-only": dict(small_max=1, bitmap_max=1),
     "narrow-cta": dict(warps_per_cta=2),
+    # every bitmap-path root is split into units taken from a shared cursor; 3 blocks, so that
+    # blocks that find the root queue empty help with roots still in progress
+    "split-steal": dict(small_max=1, split_min=2, max_blocks=3),
 }
 
 
@@ -104,7 +107,7 @@ def test_counts_match_oracle(gpu, oracle_lib, graphs, path, name, relabel):
         assert G.count(k, **PATHS[path]) == want, (k, path)
 
 
-@pytest.mark.parametrize("path", ["default", "list-only"])
+@pytest.mark.parametrize("path", ["default", "list-only", "split-steal"])
 def test_per_root_counts(gpu, oracle_lib, graphs, path):
     g = graphs["rmat-n50000"]
     G = gpu.DeviceGraph(g, relabel=True)
@@ -233,3 +236,28 @@ def test_dense_random_exercises_every_compact_width(gpu, oracle_lib):
     G = gpu.DeviceGraph(gg.cocktail_party(100))
     for k in (4, 5):
         assert G.count(k) == math.comb(100, k) * 2 ** k
+
+
+def test_heavy_edge_splitting_and_stealing(gpu, oracle_lib):
+    """Heavy roots split into edge sub-tasks (u, a_t, b) (rows above 128 members, k >= 6) and
+    stolen by blocks whose root queue is empty: dense random graphs and a graph of planted
+    40-cliques give the oracle's counts and per-root counts for every split threshold and block
+    count, and the balance timers report a span that contains the tail."""
+    dense = gg.random_small(31, 260, 0.75)
+    planted = gg.config1_er_planted(seed=5, n=3000, avg_deg=12.0, clique=40)
+    for g in (dense, planted):
+        G = gpu.DeviceGraph(g)
+        off, cols = G.dag_numpy()
+        roots = np.arange(g.n, dtype=np.uint32)
+        for k in (4, 5, 6, 7):
+            want_tot, want = oracle_lib.count_roots(off, cols, g.n, k, roots, per_root=True)
+            assert want_tot == oracle_lib.count_graph(g, k)
+            for split_min, blocks in ((2, 2), (2, 7), (150, 4), (1, 0)):
+                pr = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+                got, o = gpu.citron_count_ex(g.n, G.dag_off, G.dag_cols, k, G.ws, G.max_outdeg, pr,
+                                             small_max=1, split_min=split_min, max_blocks=blocks,
+                                             balance=True)
+                assert got == want_tot, (k, split_min, blocks)
+                assert np.array_equal(pr.cpu().numpy().view(np.uint64), want), (k, split_min, blocks)
+                span, tail = o.busy_ms[0], o.busy_ms[1]
+                assert 0.0 <= tail <= span
