@@ -4,10 +4,15 @@ workload: 2^20 vertices, edge factor 16, (a,b,c,d) = (0.57,0.19,0.19,0.05), dedu
 symmetrised, seeded.
 
 One step = for every k of the step: degree ordering (citron_order) + relabelled DAG
-(citron_build_dag) + exact count (citron_count_ex), i.e. one full order+count job per k.
-value = edges of all jobs (m undirected edges per job, all ranks) / device time of the steps.
+(citron_build_dag, with its largest row) + exact count (citron_count_ex), i.e. one full
+order+count job per k.  value = edges of all jobs (m undirected edges per job, all ranks) / device
+time of the steps.  At N = 1 the same line carries the rest of the metric, each timed on its own:
+R-MAT k = 7 (one job) and k = 8 (under a time budget), the 4M-vertex Chung-Lu graph at k = 5, 6,
+the 4,096-graph batch (graphs/s against one launch sequence per graph) and the serving loop
+(p50/p99 and requests/s at 100 and 1,000 req/s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--ks 4,5,6] [--impl ours|reference]
+                  [--extras all|none|k7,k8,chunglu,batch,serve]
 
 --impl reference times the oracle (plain C, CPU) on the host cores on a bounded sample of the
 same workload.  N > 1 (torchrun) runs independent replicas (the counting of one graph is not
@@ -33,27 +38,44 @@ sys.path.insert(0, str(ROOT))
 METRIC = "order+count edges/s at k=4..9 (exact, 1 GB300); batched graphs/s; serve p50/p99"
 UNIT = "edges/s"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-# POPC: 16 results per clock per SM (integer-pipe table for recent architectures), 152 SMs,
-# 2070 MHz maximum SM clock -> ceiling for 32-bit AND+POPC word operations
-POPC_PEAK_OPS = 16 * 152 * 2.070e9
+# Nominal ceiling of 32-bit AND+POPC word operations: 16 POPC results per clock per SM, 152 SMs,
+# 2070 MHz.  The roofline's peak is the rate citron_probe_word_ops measures on the device.
+POPC_NOMINAL_OPS = 16 * 152 * 2.070e9
+EXTRAS = ("k7", "k8", "chunglu", "batch", "serve")
+TUNED = ROOT / "paper_2112_10913_gb300" / "tuned_plans.json"
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--ks", default="4,5,6")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--cpu-budget", type=float, default=6.0, help="seconds of oracle counting per k")
+    p.add_argument("--cpu-budget", type=float, default=20.0,
+                   help="wall seconds of sampled oracle counting per k (bands in parallel processes)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="rmat20",
                    choices=["rmat20", "batch", "serve", "orderings", "list", "chunglu"],
                    help="rmat20: order+count edges/s (default); batch: 4,096-graph batched graphs/s; "
-                        "serve: request loop; orderings: degree vs core ordering; list: clique "
-                        "listing; chunglu: the 4M-vertex power-law graph, k=5..9")
+                        "serve: request loop at every rate; orderings: degree vs core ordering; "
+                        "list: clique listing; chunglu: the 4M-vertex power-law graph, k=5..")
     p.add_argument("--batch-graphs", type=int, default=4096)
-    return p.parse_args()
+    p.add_argument("--extras", default="all",
+                   help="extra measurements of the default line (N = 1 only), comma list of "
+                        + ",".join(EXTRAS) + ", or all / none")
+    p.add_argument("--k8-budget-s", type=float, default=30.0, help="time budget of the k = 8 count")
+    p.add_argument("--chunglu-ks", default="5,6")
+    p.add_argument("--retune", action="store_true", help="batch: time every plan instead of the cache")
+    return p.parse_args(argv)
+
+
+def extras_of(args) -> set:
+    if args.extras == "all":
+        return set(EXTRAS)
+    if args.extras == "none":
+        return set()
+    return {e for e in args.extras.split(",") if e in EXTRAS}
 
 
 def dist_env():
@@ -86,48 +108,149 @@ def workload():
 
 
 # ---------------------------------------------------------------------------------------------
-# CPU side: the oracle on a bounded sample
+# CPU side: the oracle (whole jobs where it finishes, else a stratified sample of roots)
+
+BANDS = [(0, 8), (8, 16), (16, 32), (32, 64), (64, 128), (128, 256), (256, 512), (512, 1 << 30)]
 
 
-def oracle_sample(g, ks, budget_s, seed=2):
-    """Oracle timing: full ordering + DAG, counting on a seeded uniform sample of roots whose
-    fraction doubles until one k's sample takes about `budget_s`; times scale by 1/fraction."""
+def oracle_order(g):
+    """The oracle's degree ordering and relabelled DAG of the whole graph: (dag, seconds)."""
     import oracle
+
+    t0 = time.perf_counter()
+    rank = oracle.degree_rank(g.off, g.n)
+    dag = oracle.dag_by_rank(g.off, g.cols, g.n, rank, True)
+    return dag, time.perf_counter() - t0
+
+
+def _band_worker(dag_off, dag_cols, n, k, plan, q):
+    """Runs in a spawned process: for every out-degree band in turn (lightest first), times the
+    oracle's count on one thread for each group of the band's sampled roots, and reports each
+    group as soon as it is done."""
+    import oracle
+
+    oracle.build()
+    # the cost of a call that counts nothing (thread start, scratch set-up): subtracted per group
+    idle = np.array([int(np.argmin(np.diff(dag_off)))], dtype=np.uint32)
+    cost = []
+    for _ in range(7):
+        t0 = time.perf_counter()
+        oracle.count_roots(dag_off, dag_cols, n, k, idle, 1)
+        cost.append(time.perf_counter() - t0)
+    q.put(("call", 0, float(np.median(cost))))
+    for band, chunks in plan:
+        for ch in chunks:
+            t0 = time.perf_counter()
+            oracle.count_roots(dag_off, dag_cols, n, k, ch, 1)
+            q.put((band, int(ch.size), time.perf_counter() - t0))
+    q.put(None)
+
+
+def oracle_stratified(dag, n, k, budget_s, seed=2, groups=4, per=16):
+    """Single-thread oracle counting time of one k, estimated from a stratified sample of roots.
+    The roots that can hold a k-clique are split into out-degree bands; every band gets `groups`
+    seeded groups of `per` roots, timed on one thread (one worker process, bands from the
+    lightest up); a band's time is its size times its mean time per sampled root
+    (inverse-probability weighting), with a standard error from the spread of its groups.
+    Sampling stops at budget_s (the worker is stopped): a band with no group done by then is left
+    out, and the estimate is then a lower bound.  Returns (seconds on one thread, standard error,
+    sampled roots, bands left out)."""
+    import multiprocessing as mp
+    import queue as queue_mod
+
     from paper_2112_10913_gb300 import graphgen as gg
+
+    dag_off, dag_cols = dag
+    outdeg = np.diff(dag_off).astype(np.int64)
+    plan, sizes, takes = [], {}, {}
+    for b, (lo, hi) in enumerate(BANDS):
+        ids = np.nonzero((outdeg >= max(k - 1, lo + 1)) & (outdeg <= hi))[0]
+        if not ids.size:
+            continue
+        ids = ids[gg.permutation(seed, 20 + b, ids.size)]
+        take = min(ids.size, per * groups)
+        plan.append((b, [c.astype(np.uint32) for c in np.array_split(ids[:take], min(groups, take)) if c.size]))
+        sizes[b], takes[b] = int(ids.size), take
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    proc = ctx.Process(target=_band_worker, args=(dag_off, dag_cols, n, k, plan, q), daemon=True)
+    proc.start()
+    done = {b: [] for b in sizes}
+    deadline = time.perf_counter() + budget_s
+    finished, call_s = False, 0.0
+    while not finished and time.perf_counter() < deadline:
+        try:
+            item = q.get(timeout=min(0.5, max(0.01, deadline - time.perf_counter())))
+        except queue_mod.Empty:
+            continue
+        if item is None:
+            finished = True
+        elif item[0] == "call":
+            call_s = item[2]
+        else:
+            done[item[0]].append((item[1], max(0.0, item[2] - call_s)))
+    if not finished:
+        proc.terminate()
+    proc.join(timeout=10)
+    est, var, sampled, missing = 0.0, 0.0, 0, []
+    for b, res in done.items():
+        if not res:
+            missing.append(BANDS[b])
+            continue
+        rates = [t / c for c, t in res]
+        sampled += sum(c for c, _ in res)
+        est += sizes[b] * float(np.mean(rates))
+        if len(rates) > 1 and takes[b] < sizes[b]:
+            var += (sizes[b] ** 2) * float(np.var(rates, ddof=1)) / len(rates)
+    return est, var ** 0.5, sampled, missing
+
+
+def cpu_baseline_obj(g, ks, budget_s, gpu_counts=None):
+    """The oracle on this host's cores for the same jobs: ordering + DAG on the whole graph;
+    counting on the whole graph, all threads, for k <= 4 (checked against the GPU's count); for
+    larger k, the single-thread time estimated from a stratified root sample (oracle_stratified)
+    over the thread count (the oracle's roots are independent tasks taken dynamically: ideal
+    scaling is assumed)."""
+    import oracle
 
     oracle.build()
     threads = oracle.default_threads()
-    t0 = time.perf_counter()
-    rank = oracle.degree_rank(g.off, g.n)
-    dag_off, dag_cols = oracle.dag_by_rank(g.off, g.cols, g.n, rank, True)
-    t_order = time.perf_counter() - t0
-    perm = gg.permutation(seed, 77, g.n).astype(np.uint32)
-    per_k, samples = {}, {}
+    dag, t_order = oracle_order(g)
+    per_k, total, se2, samples = {}, 0.0, 0.0, []
+    lower = False
     for k in ks:
-        frac = 1e-4
-        while True:
-            take = max(1, int(round(frac * g.n)))
-            roots = perm[:take]
+        if k <= 4:
             t0 = time.perf_counter()
-            oracle.count_roots(dag_off, dag_cols, g.n, k, roots, threads)
-            dt = time.perf_counter() - t0
-            if dt >= budget_s / 4 or take == g.n:
-                break
-            frac = min(1.0, frac * max(2.0, 0.5 * budget_s / max(dt, 1e-3)))
-        per_k[k] = dt * g.n / take
-        samples[k] = take
-    return dict(t_order=t_order, t_count=per_k, roots=samples, threads=threads)
-
-
-def cpu_baseline_obj(g, ks, budget_s):
-    r = oracle_sample(g, ks, budget_s)
-    total = sum(r["t_order"] + r["t_count"][k] for k in ks)
-    value = g.m * len(ks) / total
-    sample = (f"full oracle ordering+DAG ({r['t_order']:.2f} s per job); counting on a seeded uniform "
-              f"sample of roots per k ({', '.join(f'k={k}: {r['roots'][k]} of {g.n}' for k in ks)}), "
-              f"time scaled by n/sample")
-    return dict(value=value, unit=UNIT, cores=r["threads"], kind="oracle", sample=sample,
-                est_seconds_per_job={str(k): r["t_order"] + r["t_count"][k] for k in ks})
+            c = oracle.count(dag[0], dag[1], g.n, k, threads)
+            t_count = time.perf_counter() - t0
+            if gpu_counts is not None:
+                assert c == gpu_counts[k], f"oracle k={k}: {c} != GPU {gpu_counts[k]}"
+            per_k[str(k)] = dict(seconds=t_order + t_count, order_s=t_order, count_s=t_count,
+                                 count=c, count_equal_gpu=gpu_counts is not None, sample="whole graph")
+            total += t_order + t_count
+            samples.append(f"k={k} on the whole graph, all threads")
+        else:
+            t1, se1, m, missing = oracle_stratified(dag, g.n, k, budget_s)
+            scale = 1.0 / threads
+            est, se = t1 * scale, se1 * scale
+            per_k[str(k)] = dict(seconds=t_order + est, order_s=t_order, count_s=est, count_se_s=se,
+                                 single_thread_s=t1, sample=f"{m} roots stratified by out-degree",
+                                 bands_not_sampled=[list(b) for b in missing],
+                                 lower_bound=bool(missing))
+            total += t_order + est
+            se2 += se * se
+            lower = lower or bool(missing)
+            samples.append(f"k={k} from {m} roots stratified by out-degree, single-thread times "
+                           "weighted by inverse sampling probability, over the thread count"
+                           + (f" (out-degree bands {missing} not sampled within {budget_s:.0f} s: "
+                              "a lower bound on the time)" if missing else ""))
+    se = se2 ** 0.5
+    units = g.m * len(ks)
+    return dict(value=units / total, unit=UNIT, cores=threads, kind="oracle",
+                sample="oracle ordering + DAG on the whole graph per job; counting " + "; ".join(samples),
+                seconds_per_step=total, seconds_se=se,
+                seconds_is_lower_bound=lower,
+                value_1se_range=[units / (total + se), units / max(total - se, 1e-9)], per_k=per_k)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -191,8 +314,16 @@ class ClockSampler:
                     samples=len(sm))
 
 
+
 # ---------------------------------------------------------------------------------------------
 # GPU side
+
+
+def _hbm_peak() -> float:
+    try:
+        return float(json.loads((ROOT / "MEASURED_PEAKS.json").read_text())["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def run_ours(args, ks):
@@ -224,17 +355,17 @@ def run_ours(args, ks):
     ws = cg.alloc_workspace(n, arcs, max_outdeg, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
-    def job(k, timed):
-        """One order+count job; returns (count, order_ms, count_ms, kernel_ms)."""
+    def job(k, timed, **kw):
+        """One order+count job; returns (count, order_ms, count_ms, kernel_ms, opts)."""
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         cg.citron_order(n, off, rank_t, None, ws)
-        cg.citron_build_dag(n, off, cols, rank_t, dag_off, dag_cols, ws, want_max_outdeg=False)
+        mx = cg.citron_build_dag(n, off, cols, rank_t, dag_off, dag_cols, ws)
         e1.record(stream)
-        c, o = cg.citron_count_ex(n, dag_off, dag_cols, k, ws, max_outdeg, time_kernels=timed)
+        c, o = cg.citron_count_ex(n, dag_off, dag_cols, k, ws, mx, time_kernels=timed, **kw)
         e2.record(stream)
         e2.synchronize()
-        return c, e0.elapsed_time(e1), e1.elapsed_time(e2), list(o.kernel_ms)
+        return c, e0.elapsed_time(e1), e1.elapsed_time(e2), list(o.kernel_ms), o
 
     def step(timed=False):
         return [job(k, timed) for k in ks]
@@ -249,6 +380,8 @@ def run_ours(args, ks):
     # instrumented (untimed) launch per k: word operations of the bitmap kernel
     work = {k: cg.citron_count_ex(n, dag_off, dag_cols, k, ws, max_outdeg, count_work=True)[1].work_ops
             for k in ks}
+    # measured peak of the word operation on this device (registers only, all SMs)
+    peak_ops, peak_ms = cg.citron_probe_word_ops(2, 200000)
 
     clocks = ClockSampler(local_rank)
     launches0 = cg.citron_kernel_launches()
@@ -295,6 +428,7 @@ def run_ours(args, ks):
     e2e_step = statistics.mean(e2e_ms)
     if world > 1:
         e2e_step = max_over_ranks(e2e_step, dev)
+    del dbuf
 
     if rank != 0:
         return None
@@ -306,6 +440,15 @@ def run_ours(args, ks):
     achieved = work[kd] / (kern_ms / 1e3)
     order_ms = statistics.mean(r[1] for k in ks for r in per_job[k])
     order_bytes = 8 * (n + 1) + 4 * arcs + 8 * (n + 1) + 4 * (arcs // 2) + 4 * n
+    sm_mhz = clk["sm_mhz"] if clk else None
+    per_k = {str(k): {"count": per_job[k][-1][0],
+                      "order_ms": statistics.mean(r[1] for r in per_job[k]),
+                      "count_ms": statistics.mean(r[2] for r in per_job[k]),
+                      "bitmap_kernel_ms": statistics.mean(r[3][1] for r in per_job[k]),
+                      "small_kernel_ms": statistics.mean(r[3][0] for r in per_job[k]),
+                      "edges_per_s": m / ((statistics.mean(r[1] + r[2] for r in per_job[k])) / 1e3),
+                      "word_ops": work[k], "repeats": args.steps}
+             for k in ks}
     line = {
         "metric": METRIC,
         "value": value,
@@ -323,23 +466,19 @@ def run_ours(args, ks):
             "workload": f"rmat20-ef16 k={','.join(map(str, ks))}",
             "n": n, "m_undirected": m, "arcs": arcs, "max_outdeg": max_outdeg,
             "ks": ks, "counts": {str(k): c for k, c in zip(ks, ref)},
-            "step": "per k: citron_order + citron_build_dag (relabelled) + citron_count_ex",
+            "step": "per k: citron_order + citron_build_dag (relabelled, largest row) + citron_count_ex",
             "l2": "flushed between steps (256 MB write outside the step events); CSR 134 MB > L2",
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
-        "per_k": {str(k): {"count": per_job[k][-1][0],
-                           "order_ms": statistics.mean(r[1] for r in per_job[k]),
-                           "count_ms": statistics.mean(r[2] for r in per_job[k]),
-                           "bitmap_kernel_ms": statistics.mean(r[3][1] for r in per_job[k]),
-                           "small_kernel_ms": statistics.mean(r[3][0] for r in per_job[k]),
-                           "edges_per_s": m / ((statistics.mean(r[1] + r[2] for r in per_job[k])) / 1e3),
-                           "word_ops": work[k]}
-                  for k in ks},
+        "per_k": per_k,
         "roofline": {"kernel": f"k_count_mid<{kd}> (bitmap path)", "bound": "alu",
-                     "achieved": achieved / 1e12, "peak": POPC_PEAK_OPS / 1e12,
+                     "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "T word-ops/s (32-bit AND+POPC)",
-                     "frac": achieved / POPC_PEAK_OPS, "traffic": None,
-                     "peak_source": "16 POPC/clk/SM x 152 SMs x 2070 MHz (recipe unit counts and clock)"},
+                     "frac": achieved / peak_ops, "traffic": None,
+                     "peak_source": ("measured: citron_probe_word_ops (AND+POPC+add on registers, "
+                                     f"all SMs, {peak_ms:.1f} ms) before the timed steps; nominal "
+                                     f"{POPC_NOMINAL_OPS / 1e12:.2f} T/s at 2070 MHz"),
+                     "sm_mhz_median": sm_mhz},
         "roofline_order": {"kernels": "citron_order + citron_build_dag (relabelled)", "bound": "hbm",
                            "achieved": order_bytes / (order_ms / 1e3) / 1e9, "unit": "GB/s",
                            "peak": _hbm_peak(), "frac": order_bytes / (order_ms / 1e3) / 1e9 / _hbm_peak(),
@@ -351,74 +490,117 @@ def run_ours(args, ks):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    extras = extras_of(args) if world == 1 else set()
+    if "k7" in extras:
+        flush.fill_(4)
+        c, o_ms, c_ms, kms, o = job(7, True, balance=True)
+        per_k["7"] = {"count": c, "order_ms": o_ms, "count_ms": c_ms, "bitmap_kernel_ms": kms[1],
+                      "edges_per_s": m / ((o_ms + c_ms) / 1e3), "repeats": 1,
+                      "bitmap_kernel_tail_frac": o.busy_ms[1] / o.busy_ms[0] if o.busy_ms[0] else None,
+                      "note": "timed once outside the step (order + DAG + count, CUDA events)"}
+    if "k8" in extras:
+        budget = float(args.k8_budget_s)
+        t0 = time.perf_counter()
+        try:
+            c, o_ms, c_ms, _, _ = job(8, True, budget_ms=int(budget * 1000))
+            per_k["8"] = {"count": c, "order_ms": o_ms, "count_ms": c_ms,
+                          "edges_per_s": m / ((o_ms + c_ms) / 1e3), "repeats": 1}
+        except cg.CitronError as exc:
+            if exc.name != "CITRON_E_BUDGET":
+                raise
+            per_k["8"] = {"count": None, "did_not_finish_within_s": budget,
+                          "stopped_after_s": time.perf_counter() - t0,
+                          "note": "the count's time budget ran out (CITRON_E_BUDGET); no count"}
+    del flush, ws, dag_off, dag_cols, rank_t, off, cols
+    torch.cuda.empty_cache()
+    if "chunglu" in extras:
+        line["chunglu"] = chunglu_obj(cg, [int(k) for k in args.chunglu_ks.split(",") if k])
+        torch.cuda.empty_cache()
+    if "batch" in extras:
+        line["batch"] = batch_obj(args, cg)
+        torch.cuda.empty_cache()
+    if "serve" in extras:
+        line["serve"] = serve_obj(cg, rates=(100, 1000), per_rate=400)
+        torch.cuda.empty_cache()
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_obj(g, ks, args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline_obj(g, ks, args.cpu_budget,
+                                                gpu_counts={k: c for k, c in zip(ks, ref)})
     return line
 
 
-def _hbm_peak() -> float:
-    try:
-        return float(json.loads((ROOT / "MEASURED_PEAKS.json").read_text())["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        return 6800.0
+def chunglu_obj(cg, ks):
+    """The 4M-vertex Chung-Lu graph (exponent 2.1, average degree 30, degrees capped at 20,000,
+    50 planted cliques of 20-40 vertices): order + relabelled DAG + count per k, CUDA events."""
+    import torch
+
+    from paper_2112_10913_gb300 import graphgen as gg
+
+    t0 = time.perf_counter()
+    g = gg.config3_chung_lu()
+    t_gen = time.perf_counter() - t0
+    G = cg.DeviceGraph(g)
+
+    def order_dag():
+        cg.citron_order(g.n, G.off, G.rank, None, G.ws)
+        return cg.citron_build_dag(g.n, G.off, G.cols, G.rank, G.dag_off, G.dag_cols, G.ws)
+
+    t_order = _events_ms(order_dag)
+    per_k = {}
+    for k in ks:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        c, o = cg.citron_count_ex(g.n, G.dag_off, G.dag_cols, k, G.ws, G.max_outdeg, time_kernels=True,
+                                  balance=True)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        per_k[str(k)] = dict(count=c, count_ms=ms, order_ms=t_order, edges_per_s=g.m / ((ms + t_order) / 1e3),
+                             bitmap_kernel_ms=o.kernel_ms[1],
+                             bitmap_kernel_tail_frac=o.busy_ms[1] / o.busy_ms[0] if o.busy_ms[0] else None)
+    tot = sum(per_k[str(k)]["count_ms"] + t_order for k in ks)
+    return {"workload": "chunglu-4M beta=2.1 avg30 cap20000 + 50 planted cliques (seed 3)",
+            "n": g.n, "m_undirected": g.m, "max_outdeg": G.max_outdeg, "ks": ks,
+            "edges_per_s": g.m * len(ks) / (tot / 1e3), "order_dag_ms": t_order, "per_k": per_k,
+            "generation_s": t_gen}
 
 
-def run_reference(args, ks):
-    rank, _, world = dist_env()
-    if rank != 0:
-        return None
-    g = workload()
-    budget = max(1.0, min(args.cpu_budget, 120.0 / max(1, (args.steps + args.warmup) * len(ks))))
-    for _ in range(args.warmup):
-        oracle_sample(g, ks, budget)
-    times, last = [], None
-    for _ in range(args.steps):
-        r = oracle_sample(g, ks, budget)
-        times.append(sum(r["t_order"] + r["t_count"][k] for k in ks))
-        last = r
-    t = statistics.mean(times)
-    value = g.m * len(ks) / t
-    sample = (f"oracle ordering+DAG on the full graph; counting on seeded uniform root samples "
-              f"({', '.join(f'k={k}: {last['roots'][k]} roots' for k in ks)}), scaled by n/sample")
-    return {
-        "impl": "reference",
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32/u64 (exact integer)", "data": "synthetic (seeded R-MAT)",
-        "config": {"workload": f"rmat20-ef16 k={','.join(map(str, ks))}", "n": g.n, "m_undirected": g.m,
-                   "ks": ks},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["threads"], "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
+def _batch_plan(bc, args):
+    """The autotuner's plan for this batch: the cached choice for this device and batch, or a new
+    timing of the candidate plans (kept in the cache)."""
+    import torch
+
+    from paper_2112_10913_gb300.batch import tune
+
+    key = f"{torch.cuda.get_device_name()}|config4-seed4-{len(bc.ks)}graphs"
+    if args.retune and TUNED.exists():
+        known = json.loads(TUNED.read_text())
+        known.pop(key, None)
+        TUNED.write_text(json.dumps(known, indent=1))
+    return tune(bc, repeats=1, cache=TUNED, key=key), key
 
 
-def run_batch(args):
+def batch_obj(args, cg):
     """Batched graphs/s on the 4,096-graph workload: n log-uniform in [50, 50000], ER and R-MAT
     half and half, average degree U[8, 64], k U{3..7}, seed 4.  One step = degree ordering and
     DAG of the union + the batched count replayed from its CUDA graph; compared with counting
     every graph through its own launches (upload, order, DAG, count)."""
     import torch
 
-    from paper_2112_10913_gb300 import build as B
-
-    B.build()
-    import paper_2112_10913_gb300 as cg
     from paper_2112_10913_gb300 import graphgen as gg
-    from paper_2112_10913_gb300.batch import BatchCounter, tune
+    from paper_2112_10913_gb300.batch import BatchCounter
 
     t0 = time.perf_counter()
     items = gg.config4_batch_parallel(seed=4, count=args.batch_graphs)
     t_gen = time.perf_counter() - t0
     graphs, ks = [it.graph for it in items], [it.k for it in items]
     bc = BatchCounter(graphs, ks)
-    tuned = tune(bc)
+    tuned, key = _batch_plan(bc, args)
     bc.capture()
     bc.replay()
     ref = bc.result()
     torch.cuda.synchronize()
     steps = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(1):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record()
         bc.build()  # ordering + DAG of the union (synchronises once for the largest row)
@@ -430,29 +612,125 @@ def run_batch(args):
         steps.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
     order_ms = statistics.mean(a for a, _ in steps)
     count_ms = statistics.mean(b for _, b in steps)
-    # the plain path: every graph through its own launches
+    del bc
+    torch.cuda.empty_cache()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     single = [cg.DeviceGraph(g).count(k) for g, k in zip(graphs, ks)]
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t1
+    assert single == ref, "batched and one-graph counts differ"
+    return {"workload": f"{len(graphs)} graphs, n log-uniform [50,50000], ER/R-MAT, avg degree U[8,64], "
+                        "k U{3..7}, seed 4",
+            "graphs_per_s": len(graphs) / ((order_ms + count_ms) / 1e3), "unit": "graphs/s",
+            "ms_per_step": order_ms + count_ms, "steps": len(steps),
+            "order_dag_ms": order_ms, "batched_count_replay_ms": count_ms,
+            "one_launch_per_graph": {"seconds": t_single, "graphs_per_s": len(graphs) / t_single,
+                                     "counts_equal": True},
+            "speedup_vs_one_launch_per_graph": (len(graphs) / ((order_ms + count_ms) / 1e3)) / (len(graphs) / t_single),
+            "tuned_plan": {k: v for k, v in tuned.items() if k not in ("tried",)}, "plan_cache_key": key,
+            "k_histogram": {str(k): int(c) for k, c in enumerate(np.bincount(ks)) if c},
+            "generation_s": t_gen}
+
+
+def _serve_pool(per_rate):
+    from paper_2112_10913_gb300 import graphgen as gg
+
+    pool = gg.config4_batch_parallel(seed=5, count=per_rate)
+    big = [gg.config2_rmat(seed=50 + i, scale=18, edge_factor=16) for i in range(2)]
+    for j in range(0, per_rate, 50):  # 2 % of the requests
+        pool[j] = gg.BatchItem(big[(j // 50) % 2], pool[j].k)
+    return pool
+
+
+def serve_obj(cg, rates=(100, 1000), per_rate=400):
+    """The request loop (continuous batching) on Poisson arrivals at the given rates: requests
+    drawn from the batch distribution (seed 5) plus 2 % R-MAT scale-18 graphs; p50/p99 of all
+    requests and of the light lane, achieved requests/s; every count equal to the graph counted
+    alone, whose own latency is the floor."""
+    from paper_2112_10913_gb300.serve import Request, ServeConfig, ServeEngine, poisson_arrivals, summarize
+
+    pool = _serve_pool(per_rate)
+    alone, alone_ms = [], []
+    for it in pool:
+        t0 = time.perf_counter()
+        alone.append(cg.DeviceGraph(it.graph).count(it.k))
+        alone_ms.append((time.perf_counter() - t0) * 1e3)
+    cfg = ServeConfig()
+    per = {}
+    for rate in rates:
+        arrivals = poisson_arrivals(float(rate), per_rate, seed=rate)
+        reqs = [Request(i, it.graph, it.k, arrival=float(a)) for i, (it, a) in enumerate(zip(pool, arrivals))]
+        eng = ServeEngine(cfg)
+        try:
+            done = eng.run(reqs, timeout_s=600)
+        finally:
+            eng.close()
+        assert [r.count for r in sorted(done, key=lambda r: r.rid)] == alone, "serving changed a count"
+        per[str(rate)] = summarize(done)
+    return {"workload": f"{per_rate} requests per rate from the batch distribution (seed 5) + 2% R-MAT "
+                        "scale 18, Poisson arrivals",
+            "per_rate": per, "counts_equal_alone": True,
+            "alone_latency_ms": {"p50": float(np.percentile(alone_ms, 50)),
+                                 "p99": float(np.percentile(alone_ms, 99)),
+                                 "sum_s": float(sum(alone_ms) / 1e3)},
+            "config": {k: getattr(cfg, k) for k in ("slots", "max_batch_requests", "heavy_arcs",
+                                                    "heavy_sm_fraction", "hbm_budget_bytes")}}
+
+
+def run_reference(args, ks):
+    """The oracle arm: the oracle on this host's cores, on the same workload, metric and unit.
+    Every step orders the whole graph and estimates each k's counting time from a stratified
+    sample of roots sized so that the whole run ends within a few minutes."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    threads = oracle.default_threads()
+    g = workload()
+    budget = max(0.5, min(args.cpu_budget, 150.0 / max(1, (args.steps + args.warmup) * len(ks))))
+    times, last = [], None
+    for i in range(args.warmup + args.steps):
+        dag, t_order = oracle_order(g)
+        t = 0.0
+        for k in ks:
+            t1, _, sampled, _ = oracle_stratified(dag, g.n, k, budget, seed=2 + i)
+            t += t_order + t1 / threads
+        if i >= args.warmup:
+            times.append(t)
+        last = sampled
+    t = statistics.mean(times)
+    value = g.m * len(ks) / t
+    sample = (f"oracle ordering + DAG on the whole graph per job; counting time per k estimated from "
+              f"roots stratified by out-degree ({budget:.1f} s of single-thread sampling per k, "
+              f"inverse-probability weighted, divided by {threads} threads; last k: {last} roots)")
     return {
-        "metric": "batched graphs/s (exact per-graph k-clique counts)",
-        "value": len(graphs) / ((order_ms + count_ms) / 1e3),
-        "unit": "graphs/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
-        "ms_per_step": order_ms + count_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32/u64 (exact integer)", "data": "synthetic (seeded ER/R-MAT)",
-        "config": {"workload": f"batch of {len(graphs)} graphs, n log-uniform [50,50000], ER/R-MAT, "
-                               "avg degree U[8,64], k U{3..7}, seed 4",
-                   "vertices": bc.n, "arcs": bc.arcs, "max_outdeg": bc.max_outdeg,
-                   "k_histogram": {str(k): int(c) for k, c in enumerate(np.bincount(ks)) if c},
-                   "generation_s": t_gen},
-        "order_dag_ms": order_ms, "batched_count_replay_ms": count_ms,
-        "count_only_graphs_per_s": len(graphs) / (count_ms / 1e3),
-        "tuned_plan": {k: v for k, v in tuned.items() if k != "tried"}, "tuning": tuned.get("tried"),
-        "one_launch_per_graph": {"seconds": t_single, "graphs_per_s": len(graphs) / t_single,
-                                 "counts_equal": single == ref},
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32/u64 (exact integer)", "data": "synthetic (seeded R-MAT)",
+        "config": {"workload": f"rmat20-ef16 k={','.join(map(str, ks))}", "n": g.n, "m_undirected": g.m,
+                   "ks": ks},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+def run_batch(args):
+    """The batch measurement alone, as its own line."""
+    from paper_2112_10913_gb300 import build as B
+
+    B.build()
+    import paper_2112_10913_gb300 as cg
+
+    b = batch_obj(args, cg)
+    return {"metric": "batched graphs/s (exact per-graph k-clique counts)", "value": b["graphs_per_s"],
+            "unit": "graphs/s", "n_gpus": 1, "steps": b["steps"], "warmup": 1,
+            "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32/u64 (exact integer)", "data": "synthetic (seeded ER/R-MAT)",
+            "config": {"workload": b["workload"]}, "batch": b}
 
 
 def run_serve(args):
@@ -471,10 +749,7 @@ def run_serve(args):
     from paper_2112_10913_gb300.serve import Request, ServeConfig, ServeEngine, poisson_arrivals, summarize
 
     per_rate = 400
-    pool = gg.config4_batch_parallel(seed=5, count=per_rate)
-    big = [gg.config2_rmat(seed=50 + i, scale=18, edge_factor=16) for i in range(2)]
-    for j in range(0, per_rate, 50):  # 2 % of the requests
-        pool[j] = gg.BatchItem(big[(j // 50) % 2], pool[j].k)
+    pool = _serve_pool(per_rate)
     alone, alone_ms = [], []
     for it in pool:  # each request served alone (upload, order, DAG, count): the latency floor
         t0 = time.perf_counter()

@@ -83,6 +83,20 @@ citron_status citron_order(uint32_t n, const uint64_t *d_off, uint32_t *d_rank, 
                            void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * citron_order_grouped -- the degree ordering of every graph of a batch at once.  The input is
+ * the disjoint union of the graphs (d_off as for citron_order) with d_group[u] (device, n
+ * entries) = the graph of vertex u, below ngroups.  The vertices are sorted by (d_group[u], d(u),
+ * u): every graph's vertices get a contiguous range of positions, in the graph's own degree
+ * order (Sec. II, Sec. IV).  The DAG citron_build_dag relabels with this rank is therefore the
+ * concatenation of the graphs' own relabelled DAGs (ranks shifted by the graph's first
+ * position), so each graph's DAG is a contiguous slice of it.  Outputs as for citron_order.
+ * Asynchronous.
+ */
+citron_status citron_order_grouped(uint32_t n, const uint64_t *d_off, const uint32_t *d_group,
+                                   uint32_t ngroups, uint32_t *d_rank, uint32_t *d_perm, void *ws,
+                                   size_t ws_bytes, void *stream);
+
+/*
  * citron_core_order -- the core ordering of Algorithm OrdCore (Sec. III), computed in
  * synchronous peeling rounds: each round raises a level to the smallest remaining degree (it
  * never falls) and removes, together, every remaining vertex whose remaining degree is at most

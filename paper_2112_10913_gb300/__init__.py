@@ -34,6 +34,7 @@ EXPORTS = (
     "citron_workspace_bytes",
     "citron_validate",
     "citron_order",
+    "citron_order_grouped",
     "citron_core_order",
     "citron_build_dag",
     "citron_count",
@@ -116,6 +117,8 @@ def lib() -> ctypes.CDLL:
     L.citron_validate.restype = i32
     L.citron_order.argtypes = [u32, vp, vp, vp, vp, sz, vp]
     L.citron_order.restype = i32
+    L.citron_order_grouped.argtypes = [u32, vp, vp, u32, vp, vp, vp, sz, vp]
+    L.citron_order_grouped.restype = i32
     L.citron_core_order.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.citron_core_order.restype = i32
     L.citron_build_dag.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
@@ -202,6 +205,12 @@ def citron_validate(n: int, off, cols, ws, stream=None) -> int:
 def citron_order(n: int, off, rank, perm=None, ws=None, stream=None):
     _check(lib().citron_order(n, _dptr(off), _dptr(rank), _dptr(perm), _dptr(ws), _nbytes(ws),
                               _stream(stream)), "citron_order")
+
+
+def citron_order_grouped(n: int, off, group, ngroups: int, rank, perm=None, ws=None, stream=None):
+    """Degree ordering of a disjoint union of graphs, graph by graph: (group, degree, id)."""
+    _check(lib().citron_order_grouped(n, _dptr(off), _dptr(group), ngroups, _dptr(rank), _dptr(perm),
+                                      _dptr(ws), _nbytes(ws), _stream(stream)), "citron_order_grouped")
 
 
 def citron_core_order(n: int, off, cols, rank, perm=None, ws=None, stream=None) -> tuple[int, int]:

@@ -14,6 +14,9 @@ size_t order_ws_bytes(uint32_t n);
 size_t dag_ws_bytes(uint32_t n, uint64_t arcs);
 cudaError_t launch_order(uint32_t n, const uint64_t *off, uint32_t *rank, uint32_t *perm,
                          uint32_t *err, Carver &c, cudaStream_t st);
+cudaError_t launch_order_grouped(uint32_t n, const uint64_t *off, const uint32_t *group,
+                                 uint32_t ngroups, uint32_t *rank, uint32_t *perm, uint32_t *err,
+                                 Carver &c, cudaStream_t st);
 cudaError_t launch_build_dag(uint32_t n, uint64_t arcs, const uint64_t *off, const uint32_t *cols,
                              const uint32_t *rank, uint64_t *dag_off, uint32_t *dag_cols,
                              uint32_t *d_max_outdeg, uint32_t *err, Carver &c, cudaStream_t st,
@@ -206,6 +209,17 @@ citron_status citron_order(uint32_t n, const uint64_t *d_off, uint32_t *d_rank, 
     if (!ws_ok(ws, ws_bytes, kHeader + order_ws_bytes(n))) return CITRON_E_WORKSPACE;
     Carver c((char *)ws + kHeader, ws_bytes - kHeader);
     return from_cuda(launch_order(n, d_off, d_rank, d_perm, err_word(ws), c, (cudaStream_t)stream));
+}
+
+citron_status citron_order_grouped(uint32_t n, const uint64_t *d_off, const uint32_t *d_group,
+                                   uint32_t ngroups, uint32_t *d_rank, uint32_t *d_perm, void *ws,
+                                   size_t ws_bytes, void *stream)
+{
+    if (n == 0xffffffffu || !d_off || (n && (!d_rank || !d_group))) return CITRON_E_INVALID;
+    if (!ws_ok(ws, ws_bytes, kHeader + order_ws_bytes(n))) return CITRON_E_WORKSPACE;
+    Carver c((char *)ws + kHeader, ws_bytes - kHeader);
+    return from_cuda(launch_order_grouped(n, d_off, d_group, ngroups, d_rank, d_perm, err_word(ws), c,
+                                          (cudaStream_t)stream));
 }
 
 citron_status citron_core_order(uint32_t n, uint64_t arcs, const uint64_t *d_off,

@@ -65,7 +65,8 @@ struct Budget {
             t0 = atomicCAS(clock0, 0ull, now);
             if (t0 == 0) t0 = now;
         }
-        if (now - t0 <= ns) return false;
+        // another block may have started the clock a moment after this one read the timer
+        if (now <= t0 || now - t0 <= ns) return false;
         set_error(err, kDevBudget);
         return true;
     }

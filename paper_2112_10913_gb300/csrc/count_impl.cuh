@@ -964,11 +964,15 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
                 }
                 __syncthreads();
             }
-            uint32_t *cursor = (s_slot != kNoHelpSlot && (owner || s_task == 0)) ? &ht.slots[s_slot].cursor
-                                                                                   : &s_task;
+            // the units of a published heavy root come from its slot's cursor in global memory,
+            // the others from the block's counter in shared memory
+            uint32_t *gcursor = (s_slot != kNoHelpSlot && (owner || s_task == 0)) ? &ht.slots[s_slot].cursor
+                                                                                    : nullptr;
             for (;;) {
                 uint32_t i = 0;
-                if (lane == 0) i = heavy && budget.over(err) ? U : atomicAdd(cursor, 1u);
+                if (lane == 0)
+                    i = heavy && budget.over(err) ? U
+                                                  : (gcursor ? atomicAdd(gcursor, 1u) : atomicAdd(&s_task, 1u));
                 i = __shfl_sync(kFull, i, 0);
                 if (i >= U) break;
                 uint32_t t = i, j = 0;

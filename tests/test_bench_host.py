@@ -1,0 +1,25 @@
+"""Host logic of bench.py, on the CPU: the extras switch and the oracle's stratified root sample
+(the CPU baseline's estimator), whose bands cover every root that can hold a k-clique."""
+import numpy as np
+
+import bench
+import oracle
+from paper_2112_10913_gb300 import graphgen as gg
+
+
+def test_extras_switch():
+    assert bench.extras_of(bench.parse([])) == set(bench.EXTRAS)
+    assert bench.extras_of(bench.parse(["--extras", "none"])) == set()
+    assert bench.extras_of(bench.parse(["--extras", "k7,serve,bogus"])) == {"k7", "serve"}
+
+
+def test_stratified_sample_covers_the_eligible_roots(oracle_lib):
+    g = gg.small_rmat(5, 3000, 12.0)
+    dag, _ = bench.oracle_order(g)
+    outdeg = np.diff(dag[0])
+    for k in (4, 5):
+        eligible = int((outdeg >= k - 1).sum())
+        # groups as large as the bands, within a generous budget: every band is sampled completely
+        est, se, sampled, missing = bench.oracle_stratified(dag, g.n, k, budget_s=120, per=10 ** 6)
+        assert sampled == eligible and not missing
+        assert est > 0 and se == 0.0

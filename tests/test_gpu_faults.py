@@ -118,3 +118,16 @@ def test_batched_overflow_reported_through_the_workspace(gpu, faults):
     faults()
     bc.launch()
     assert bc.result() == want
+
+
+def test_count_time_budget(gpu):
+    """A count given a time budget stops taking work once the budget has run out and reports
+    CITRON_E_BUDGET; the next count, with a budget it meets, is exact."""
+    g = gg.config2_rmat(seed=9, scale=18, edge_factor=16)
+    G = gpu.DeviceGraph(g)
+    want = G.count(6)
+    with pytest.raises(gpu.CitronError) as e:
+        G.count(6, budget_ms=1)
+    assert _status(e) == "CITRON_E_BUDGET"
+    assert G.count(6, budget_ms=600000) == want
+    assert G.count(6) == want
