@@ -22,4 +22,4 @@ def test_stratified_sample_covers_the_eligible_roots(oracle_lib):
         # groups as large as the bands, within a generous budget: every band is sampled completely
         est, se, sampled, missing = bench.oracle_stratified(dag, g.n, k, budget_s=120, per=10 ** 6)
         assert sampled == eligible and not missing
-        assert est > 0 and se == 0.0
+        assert est >= 0.0 and se == 0.0  # a tiny graph may cost no more than the calls themselves
