@@ -197,12 +197,12 @@ typedef struct {
     uint64_t *d_per_root;    /* in: optional device array of n uint64, as in citron_count */
     uint64_t work_ops;       /* out: 32-bit AND+POPC word operations of the bitmap path */
     float kernel_ms[3];      /* out: device ms of the warp-register, bitmap, sorted-list kernels */
-    uint32_t split_min;      /* in: bitmap-path roots of at least this out-degree share their work
-                                with idle blocks (heavy-edge splitting, Sec. VII-C): their edge
-                                tasks -- and for k >= 6 the sub-tasks (u, a_t, b) of rows above
-                                128 members -- are taken from a global cursor, which blocks that
-                                find the root queue empty join after rebuilding the root's
-                                subgraph.  0: default (384); 1: never; else the threshold */
+    uint32_t split_min;      /* in: for k >= 6, bitmap-path roots of at least this out-degree
+                                share their work with idle blocks (heavy-edge splitting,
+                                Sec. VII-C): their edge tasks, and the sub-tasks (u, a_t, b) of
+                                rows above 128 members, are taken from a global cursor, which
+                                blocks that find the root queue empty join after rebuilding the
+                                root's subgraph.  0: default (384); 1: never; else the threshold */
     float busy_ms[2];        /* out (CITRON_COUNT_BALANCE): bitmap kernel's span from the first
                                 block start to the last block end, and its tail from the first
                                 block end to the last */
@@ -253,6 +253,22 @@ citron_status citron_count_batch(uint32_t n, const uint64_t *d_dag_off, const ui
                                  const uint32_t *d_group_k, uint32_t ngroups, uint32_t kmask,
                                  uint32_t max_outdeg, const citron_count_opts *opts,
                                  uint64_t *d_counts, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * citron_dag_append -- copies the DAG of one graph into another DAG at a new place: the rows
+ * src_row .. src_row+n-1 of a source DAG (d_src_off holds those rows' n+1 offsets into
+ * d_src_cols; the columns are ids of the source's id space) become rows dst_row .. dst_row+n-1 of
+ * the destination, whose arcs start at dst_arc:
+ *   d_dst_off[i] = d_src_off[i] - d_src_off[0] + dst_arc            (i = 0..n, n+1 entries)
+ *   d_dst_cols[dst_arc + e] = d_src_cols[d_src_off[0] + e] - src_row + dst_row
+ * (the graph's arcs must point inside its own rows, as every graph of a disjoint union does).
+ * With it a batch is assembled from the DAGs of graphs counted before (kept on the device by a
+ * serving loop) without ordering them again, and a graph's DAG is cut out of a batch's union
+ * DAG.  The paper has no counterpart: this is data movement for batching.  Asynchronous.
+ */
+citron_status citron_dag_append(uint32_t n, const uint64_t *d_src_off, const uint32_t *d_src_cols,
+                                uint32_t src_row, uint64_t *d_dst_off, uint32_t *d_dst_cols,
+                                uint32_t dst_row, uint64_t dst_arc, void *stream);
 
 /* Synchronises `stream` and reports (then clears) the device error word of the workspace:
  * errors recorded by asynchronous calls such as citron_count_batch or citron_build_dag. */

@@ -46,6 +46,7 @@ EXPORTS = (
     "citron_count_noalloc",
     "citron_count_batch",
     "citron_workspace_status",
+    "citron_dag_append",
     "citron_set_faults",
     "citron_probe_word_ops",
 )
@@ -141,6 +142,8 @@ def lib() -> ctypes.CDLL:
     L.citron_count_batch.restype = i32
     L.citron_workspace_status.argtypes = [vp, vp]
     L.citron_workspace_status.restype = i32
+    L.citron_dag_append.argtypes = [u32, vp, vp, u32, vp, vp, u32, u64, vp]
+    L.citron_dag_append.restype = i32
     L.citron_set_faults.argtypes = [vp]
     L.citron_set_faults.restype = i32
     L.citron_probe_word_ops.argtypes = [u32, u32, vp, vp, vp]
@@ -297,6 +300,15 @@ def citron_probe_word_ops(blocks_per_sm: int = 2, iters: int = 200000, stream=No
     _check(lib().citron_probe_word_ops(blocks_per_sm, iters, ctypes.byref(ops), ctypes.byref(ms),
                                        _stream(stream)), "citron_probe_word_ops")
     return float(ops.value), float(ms.value)
+
+
+def citron_dag_append(n: int, src_off, src_cols, src_row: int, dst_off, dst_cols, dst_row: int,
+                      dst_arc: int, stream=None):
+    """Copy the DAG rows src_row.. (src_off: their n+1 offsets) to rows dst_row.., arcs from
+    dst_arc, offsets re-based and column ids shifted (asynchronous)."""
+    _check(lib().citron_dag_append(n, _dptr(src_off), _dptr(src_cols), src_row, _dptr(dst_off),
+                                   _dptr(dst_cols), dst_row, dst_arc, _stream(stream)),
+           "citron_dag_append")
 
 
 def citron_workspace_status(ws, stream=None):

@@ -50,6 +50,9 @@ citron_faults injected_faults()
     return g_faults;
 }
 cudaError_t seed_totals(unsigned long long *p, uint32_t count, cudaStream_t s);
+cudaError_t launch_dag_append(uint32_t n, const uint64_t *src_off, const uint32_t *src_cols,
+                              uint32_t src_row, uint64_t *dst_off, uint32_t *dst_cols,
+                              uint32_t dst_row, uint64_t dst_arc, cudaStream_t s);
 cudaError_t launch_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t k,
                                     unsigned long long *per_root, cudaStream_t s);
 cudaError_t run_count_async(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_cols, uint32_t k,
@@ -391,6 +394,15 @@ citron_status citron_count_batch(uint32_t n, const uint64_t *d_dag_off, const ui
                             sm_count());
     }
     return from_cuda(e);
+}
+
+citron_status citron_dag_append(uint32_t n, const uint64_t *d_src_off, const uint32_t *d_src_cols,
+                                uint32_t src_row, uint64_t *d_dst_off, uint32_t *d_dst_cols,
+                                uint32_t dst_row, uint64_t dst_arc, void *stream)
+{
+    if (!d_src_off || !d_dst_off || (n && (!d_src_cols || !d_dst_cols))) return CITRON_E_INVALID;
+    return from_cuda(launch_dag_append(n, d_src_off, d_src_cols, src_row, d_dst_off, d_dst_cols,
+                                       dst_row, dst_arc, (cudaStream_t)stream));
 }
 
 citron_status citron_set_faults(const citron_faults *faults)

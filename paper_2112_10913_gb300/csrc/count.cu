@@ -153,6 +153,21 @@ __global__ void k_per_root_trivial(uint32_t n, const uint64_t *dag_off, uint32_t
     if (u < n) per_root[u] = k == 1 ? 1ull : (unsigned long long)(dag_off[u + 1] - dag_off[u]);
 }
 
+// Copy of a DAG slice to a new place: offsets re-based, column ids shifted (citron_dag_append).
+// Grid-stride over the n + 1 offsets, then over the arcs.
+__global__ void k_dag_append(uint32_t n, const uint64_t *__restrict__ src_off,
+                             const uint32_t *__restrict__ src_cols, uint32_t src_row,
+                             uint64_t *__restrict__ dst_off, uint32_t *__restrict__ dst_cols,
+                             uint32_t dst_row, uint64_t dst_arc)
+{
+    const uint64_t base = src_off[0];
+    const uint64_t arcs = src_off[n] - base;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint64_t i = i0; i <= n; i += stride) dst_off[i] = src_off[i] - base + dst_arc;
+    for (uint64_t e = i0; e < arcs; e += stride) dst_cols[dst_arc + e] = src_cols[base + e] - src_row + dst_row;
+}
+
 // Sets count uint64 values (the injected seed of the device totals, tests only).
 __global__ void k_fill_u64(unsigned long long *p, uint32_t count, unsigned long long v)
 {
@@ -165,6 +180,15 @@ __global__ void k_fill_u64(unsigned long long *p, uint32_t count, unsigned long 
 namespace citron_host {
 
 using namespace citron;
+
+cudaError_t launch_dag_append(uint32_t n, const uint64_t *src_off, const uint32_t *src_cols,
+                              uint32_t src_row, uint64_t *dst_off, uint32_t *dst_cols,
+                              uint32_t dst_row, uint64_t dst_arc, cudaStream_t s)
+{
+    k_dag_append<<<304, 256, 0, s>>>(n, src_off, src_cols, src_row, dst_off, dst_cols, dst_row, dst_arc);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 // Seeds `count` device totals with the injected count_seed (no-op in normal operation).
 cudaError_t seed_totals(unsigned long long *p, uint32_t count, cudaStream_t s)

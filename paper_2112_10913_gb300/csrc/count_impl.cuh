@@ -811,8 +811,8 @@ __device__ __forceinline__ uint32_t pick_help_slot(const HelpTable &ht, int lane
 // (row i = V(g_u) ∩ N+(a_i), Algorithm GenSub-CITRON by sorted-list intersection) and its warps
 // count the (K-2)-cliques of every row.
 //   D < split_min: the rows (edge tasks (u, a_t)) are taken from a counter in shared memory.
-//   D >= split_min (heavy roots, K >= 4): the root's work is a space of units -- one per edge task,
-//       or, for K >= 6, one per member b of a row of more than 128 members (the edge sub-task
+//   D >= split_min (heavy roots, K >= 6): the root's work is a space of units -- one per edge
+//       task, or one per member b of a row of more than 128 members (the edge sub-task
 //       (u, a_t, b): the (K-3)-cliques of row_t ∧ row_b) -- taken from a cursor in a global
 //       table.  Blocks that find the root queue empty pick the published heavy root with the
 //       most units left, rebuild its rows and take units from the same cursor (work stealing
@@ -862,7 +862,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
         const bool owner = idx < nlist;
         if (!owner) {
             queue_empty = true;
-            if (K < 4 || ht.slots == nullptr || idx == 0xfffffffeu) break;
+            if (K < 6 || ht.slots == nullptr || idx == 0xfffffffeu) break;
             if (w == 0) {
                 const uint32_t sl = pick_help_slot(ht, lane);
                 if (lane == 0) {
@@ -880,7 +880,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
             if (threadIdx.x == 0) set_error(err, kDevBadInput);
             break;
         }
-        const bool heavy = K >= 4 && (!owner || D >= split_min);
+        const bool heavy = K >= 6 && (!owner || D >= split_min);
         const uint32_t W = (D + 31) >> 5, RS = W | 1;
         for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) sL[i] = dag_cols[base + i];
         if (K > 3)
@@ -968,13 +968,19 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
             // the others from the block's counter in shared memory
             uint32_t *gcursor = (s_slot != kNoHelpSlot && (owner || s_task == 0)) ? &ht.slots[s_slot].cursor
                                                                                     : nullptr;
-            for (;;) {
-                uint32_t i = 0;
+            // a warp claims its next unit before it works on the current one, so that the
+            // atomic's round trip (global memory for a published heavy root) overlaps the work
+            auto claim = [&]() -> uint32_t {
+                uint32_t v = 0;
                 if (lane == 0)
-                    i = heavy && budget.over(err) ? U
-                                                  : (gcursor ? atomicAdd(gcursor, 1u) : atomicAdd(&s_task, 1u));
-                i = __shfl_sync(kFull, i, 0);
+                    v = heavy && budget.over(err) ? U : (gcursor ? atomicAdd(gcursor, 1u) : atomicAdd(&s_task, 1u));
+                return v;
+            };
+            uint32_t next_i = claim();
+            for (;;) {
+                const uint32_t i = __shfl_sync(kFull, next_i, 0);
                 if (i >= U) break;
+                next_i = claim();
                 uint32_t t = i, j = 0;
                 bool whole = true;
                 if (heavy) {

@@ -84,3 +84,24 @@ def test_block_cap_keeps_counts(gpu):
         for cap in (1, 7, 40):
             assert dg.count(k, max_blocks=cap) == want, (k, cap)
             assert dg.count(k, max_blocks=cap, small_max=8, bitmap_max=64) == want, (k, cap)
+
+
+def test_repeat_queries_use_the_device_cache(gpu, oracle_lib):
+    """A graph queried again (another k) is served from its DAG kept on the device: no upload, no
+    ordering; the counts equal the graph counted alone.  The cache never exceeds its bytes."""
+    from paper_2112_10913_gb300.serve import Request, ServeConfig, ServeEngine
+
+    pool = gg.config4_batch(seed=21, count=10, n_range=(60, 1500))
+    first = [Request(i, it.graph, 3, arrival=0.0) for i, it in enumerate(pool)]
+    again = [Request(100 + i, it.graph, 3 + i % 4, arrival=0.05) for i, it in enumerate(pool)]
+    eng = ServeEngine(ServeConfig(slots=2, max_batch_requests=4, cache_bytes=256 << 20))
+    try:
+        done1 = eng.run(first, timeout_s=120)
+        done2 = eng.run(again, timeout_s=120)
+    finally:
+        eng.close()
+    assert not any(r.cached for r in done1)
+    assert all(r.cached for r in done2)
+    assert eng.cache.hits == len(again) and eng.cache.bytes <= 256 << 20
+    for r in done1 + done2:
+        assert r.count == gpu.DeviceGraph(r.graph).count(r.k) == oracle_lib.count_graph(r.graph, r.k), r.rid

@@ -37,7 +37,7 @@ def engine_cls(monkeypatch):
             self.rec_lock = threading.Lock()
             super().__init__(*a, **kw)
 
-        def _run_batch(self, batch, stream, max_blocks=0):
+        def _run_batch(self, batch, stream, max_blocks=0, **kw):
             with self.rec_lock:
                 self.seen.append(([r.rid for r in batch], stream.priority, max_blocks))
                 self.max_bytes = max(self.max_bytes, self.in_flight_bytes)
@@ -54,7 +54,7 @@ def test_lanes_batches_and_answers(engine_cls):
     reqs = [serve.Request(i, g, 3 + i % 3, arrival=0.0005 * i) for i, g in enumerate(light)]
     reqs += [serve.Request(100 + j, heavy, 4, arrival=0.004 * j) for j in range(3)]
     cfg = serve.ServeConfig(slots=2, max_batch_requests=4, heavy_arcs=heavy.arcs, heavy_slots=1,
-                            heavy_sm_fraction=0.5)
+                            heavy_sm_fraction=0.5, cache_bytes=0)
     eng = Recording(cfg, device="cuda:0")
     try:
         done = eng.run(reqs, timeout_s=60)
@@ -91,7 +91,8 @@ def test_admission_keeps_the_footprint_under_budget(engine_cls):
     one = serve.footprint_bytes(400, arcs)
     extra = serve.footprint_bytes(800, 2 * arcs) - one
     budget = one + extra // 2  # room for one request in flight, never two
-    cfg = serve.ServeConfig(slots=3, max_batch_requests=8, hbm_budget_bytes=budget, heavy_arcs=0)
+    cfg = serve.ServeConfig(slots=3, max_batch_requests=8, hbm_budget_bytes=budget, heavy_arcs=0,
+                            cache_bytes=0)
     eng = Recording(cfg, device="cuda:0")
     try:
         done = eng.run([serve.Request(i, g, 3, arrival=0.0) for i, g in enumerate(graphs)],
@@ -111,7 +112,7 @@ def test_slot_handoff_never_loses_a_request(engine_cls):
     serve, _ = engine_cls
 
     class Instant(serve.ServeEngine):
-        def _run_batch(self, batch, stream, max_blocks=0):
+        def _run_batch(self, batch, stream, max_blocks=0, **kw):
             return [r.k for r in batch]
 
         def _release(self, slot, batch):
@@ -128,3 +129,17 @@ def test_slot_handoff_never_loses_a_request(engine_cls):
         eng.close()
     assert len(done) == len(reqs) and all(r.count == 3 for r in done)
     assert len({r.batch for r in done}) == len(reqs)
+
+
+def test_dag_cache_keeps_the_recent_graphs_within_its_bytes():
+    from paper_2112_10913_gb300.serve import DagCache
+
+    c = DagCache(100)
+    c.put("a", (1,), 40)
+    c.put("b", (2,), 40)
+    assert c.get("a")[0] == 1  # "a" is now the most recent
+    c.put("c", (3,), 40)       # evicts "b", the least recently used
+    assert c.get("b") is None and c.get("a")[0] == 1 and c.get("c")[0] == 3
+    assert c.bytes == 80
+    c.put("huge", (4,), 1000)  # larger than the cache: not kept
+    assert c.get("huge") is None
