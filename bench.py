@@ -668,6 +668,8 @@ def serve_obj(cg, rates=(100, 1000), per_rate=400):
             eng.close()
         assert [r.count for r in sorted(done, key=lambda r: r.rid)] == alone, "serving changed a count"
         per[str(rate)] = summarize(done)
+        per[str(rate)]["host_ms_by_phase"] = {k: round(v, 1) for k, v in eng.phase_ms.items()}
+        per[str(rate)]["cache_hits"] = eng.cache.hits if eng.cache else 0
     return {"workload": f"{per_rate} requests per rate from the batch distribution (seed 5) + 2% R-MAT "
                         "scale 18, Poisson arrivals",
             "per_rate": per, "counts_equal_alone": True,
@@ -767,6 +769,8 @@ def run_serve(args):
             eng.close()
         assert [r.count for r in sorted(done, key=lambda r: r.rid)] == alone, "serving changed a count"
         results[str(rate)] = summarize(done)
+        results[str(rate)]["host_ms_by_phase"] = {k: round(v, 1) for k, v in eng.phase_ms.items()}
+        results[str(rate)]["cache_hits"] = eng.cache.hits if eng.cache else 0
     top = results["5000"]
     return {
         "metric": "serve p50/p99 latency and requests/s (exact counts, continuous batching)",

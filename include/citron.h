@@ -49,6 +49,10 @@ typedef enum {
 /* Human-readable name of a status code (static string, never NULL). */
 const char *citron_status_str(citron_status s);
 
+/* Name of the CUDA runtime error behind the most recent CITRON_E_CUDA returned to this thread
+ * (static string, never NULL; "none" when there was none). */
+const char *citron_last_cuda_error(void);
+
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int citron_version(void);
 

@@ -12,7 +12,8 @@
  *   2. degree ordering: u before v iff (d(u), u) < (d(v), v)            (Sec. II, Sec. IV)
  *   3. DAG by Algorithm "GenOrdering": count kept arcs, prefix sum, fill (Sec. IV)
  *   4. counting by the kClist recursion "Counting" (Sec. III), with CITRON's subgraph build by
- *      sorted-set intersection (Sec. V-B), the prune "fewer vertices than still needed"
+ *      sorted-set intersection (Sec. V-B), the prune of candidate sets too small to hold the
+ *      clique size still needed
  *      (Sec. V-B, other optimizations) and the penultimate-level shortcut that only adds
  *      subgraph degrees (Sec. V-B, last paragraph; Counting's l = 2 branch).
  *   Also: core ordering by Algorithm "OrdCore" (Matula-Beck smallest-last, Sec. III) and the DAG
@@ -237,7 +238,7 @@ typedef struct {
 } dag_t;
 
 /* |A ∩ B| and, when out != NULL, the intersection itself, by a merge of two sorted lists
- * (Sec. V-B: "set intersections between ... sorted neighbor arrays"). */
+ * (the intersections of sorted neighbour lists of Sec. V-B). */
 static uint32_t intersect(const uint32_t *a, uint32_t na, const uint32_t *b, uint64_t nb,
                           uint32_t *out)
 {

@@ -30,6 +30,7 @@ STATUS = {
 # Every function the C ABI exports (checked against include/citron.h by the tests).
 EXPORTS = (
     "citron_status_str",
+    "citron_last_cuda_error",
     "citron_version",
     "citron_workspace_bytes",
     "citron_validate",
@@ -92,7 +93,10 @@ class CitronError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
         self.name = STATUS.get(code, f"status {code}")
-        super().__init__(f"{where}: {self.name}")
+        detail = ""
+        if self.name == "CITRON_E_CUDA" and _lib is not None:
+            detail = f" ({_lib.citron_last_cuda_error().decode()})"
+        super().__init__(f"{where}: {self.name}{detail}")
 
 
 _lib = None
@@ -110,6 +114,8 @@ def lib() -> ctypes.CDLL:
     vp, u32, u64, sz, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_int
     L.citron_status_str.argtypes = [i32]
     L.citron_status_str.restype = ctypes.c_char_p
+    L.citron_last_cuda_error.argtypes = []
+    L.citron_last_cuda_error.restype = ctypes.c_char_p
     L.citron_version.argtypes = []
     L.citron_version.restype = i32
     L.citron_workspace_bytes.argtypes = [u32, u64, u32]

@@ -89,6 +89,8 @@ int sm_count()
 
 uint32_t *err_word(void *ws) { return (uint32_t *)ws; }
 
+thread_local const char *t_last_cuda_error = "none";
+
 citron_status from_cuda(cudaError_t e)
 {
     if (e == cudaSuccess) return CITRON_OK;
@@ -96,6 +98,7 @@ citron_status from_cuda(cudaError_t e)
         cudaGetLastError();
         return CITRON_E_WORKSPACE;
     }
+    t_last_cuda_error = cudaGetErrorName(e);
     return CITRON_E_CUDA;
 }
 
@@ -153,7 +156,9 @@ const char *citron_status_str(citron_status s)
     return "unknown status";
 }
 
-int citron_version(void) { return 100; }
+int citron_version(void) { return 200; }
+
+const char *citron_last_cuda_error(void) { return t_last_cuda_error; }
 
 static bool plan_from_opts(const citron_count_opts *opts, CountPlan &plan)
 {

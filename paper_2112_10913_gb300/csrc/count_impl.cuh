@@ -1177,8 +1177,15 @@ static cudaError_t launch_mid(uint32_t grid_cap, uint32_t block_cap, uint32_t dc
                               int num_sms)
 {
     cudaError_t e;
+    // the attribute is an upper bound on the launches' dynamic shared memory; it is always set to
+    // the device's largest value, because host threads that count concurrently would otherwise
+    // overwrite each other's smaller setting between the set and the launch
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    if ((size_t)(optin - 1024) < smem) return cudaErrorInvalidValue;
     if ((e = cudaFuncSetAttribute(k_count_mid<K, WORK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)))
+                                  optin - 1024)))
         return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_mid<K, WORK>, warps * 32,

@@ -296,8 +296,12 @@ static cudaError_t launch_list_k(uint32_t n, const uint64_t *dag_off, const uint
                                  uint32_t *err, cudaStream_t st, int num_sms)
 {
     const size_t smem = list_smem(dcap, K);
-    cudaError_t e = cudaFuncSetAttribute(k_list<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    // a fixed upper bound (the device's largest), so that concurrent callers cannot undercut it
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!e && (size_t)(optin - 1024) < smem) e = cudaErrorInvalidValue;
+    if (!e) e = cudaFuncSetAttribute(k_list<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
     int per_sm = 0;
     if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_list<K>, kLsWarps * 32, smem);
     if (e) return e;

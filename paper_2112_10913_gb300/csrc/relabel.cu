@@ -6,22 +6,23 @@
 // (Sec. II, Sec. IV) in rank space, where every local subgraph of the counting phase is
 // upper-triangular.
 //
-// Four launches, none of which waits on another block:
+// Four launches; no block waits on another, and only the scan waits on earlier tiles:
 //   k_rl_prologue : rowlen[r] = 0 and perm[rank[u]] = u (the vertex of each rank);
-//   k_rl_keep     : one pass over the arcs in tiles of 4096.  Per arc u->v the keep-test
-//                   rank[v] > rank[u] (the rank gathers of a tile are all in flight before any
-//                   is used); the kept ranks of each row are compacted IN the row's own input
-//                   range (kept[off[u] ..]), so no global prefix is needed.  Every (row, tile)
-//                   piece takes its place in the row with one atomicAdd on rowlen[rank[u]],
-//                   which ends up holding the row's out-degree in rank order;
+//   k_rl_keep     : one pass over the arcs, one chunk of 512 arcs per warp and no block-wide
+//                   barrier.  Per arc u->v the keep-test rank[v] > rank[u] (the 16 rank gathers
+//                   of a lane are all in flight before any is used); the kept ranks of each row
+//                   are placed IN the row's own input range (kept[off[u] ..]), so no global
+//                   prefix is needed: a warp-aggregated shared counter per row gives each kept
+//                   arc its place in its row piece, and every (row, chunk) piece takes its place
+//                   in the row with one atomicAdd on rowlen[rank[u]], which ends up holding the
+//                   row's out-degree in rank order;
 //   k_scan_rowlen : dag_off = exclusive prefix of rowlen (single pass, decoupled look-back) and
 //                   the largest row;
-//   k_rl_fill     : rows in RANK order, 256 per step: each row's kept ranks are gathered from its
-//                   input range into shared memory at their output position, sorted there
-//                   (rows of <= 32 by counting the smaller entries, <= 512 by one warp's
-//                   register bitonic sort) and the step's output range dag_cols[dag_off[r0] ..
-//                   dag_off[r0 + 256]) is written out contiguously; rows above 512 are listed
-//                   for k_rl_fill_long (one block per row).
+//   k_rl_fill     : rows in RANK order, one row per lane: a row of <= 32 entries goes through
+//                   the lane's own shared-memory slots, each entry to its place (the number of
+//                   smaller entries); rows of 33..512 entries are sorted by the whole warp in
+//                   registers (bitonic); longer rows are listed for k_rl_fill_long (one block
+//                   per row).
 // The kernels after k_rl_keep return at once when the error word is set: offsets computed
 // after an error are not trusted.
 #include <cuda_runtime.h>
@@ -31,11 +32,6 @@
 
 namespace citron {
 
-constexpr int kKeThreads = 256;
-constexpr int kKeItems = 16;
-constexpr uint32_t kKeTile = kKeThreads * kKeItems;  // arcs per tile of k_rl_keep
-constexpr uint32_t kKeRowCap = 2048;                 // row offsets cached in shared memory
-constexpr int32_t kNoSlot = INT32_MIN;               // a row piece that may not be written
 
 // rowlen[r] = 0 for every rank, perm[rank[u]] = u.
 __global__ void k_rl_prologue(uint32_t n, const uint32_t *__restrict__ rank, uint32_t *rowlen,
@@ -49,44 +45,34 @@ __global__ void k_rl_prologue(uint32_t n, const uint32_t *__restrict__ rank, uin
     else set_error(err, kDevBadInput);
 }
 
-// Number of kept arcs before tile position x (0 <= x <= 4096) from the per-thread prefix and
-// keep masks of the tile.
-__device__ __forceinline__ uint32_t tile_prefix(const uint32_t *s_pref, const uint16_t *s_mask,
-                                                uint32_t x)
-{
-    const uint32_t q = x / kKeItems, b = x % kKeItems;
-    if (q >= (uint32_t)kKeThreads) return s_pref[kKeThreads];
-    return s_pref[q] + __popc((uint32_t)s_mask[q] & ((1u << b) - 1u));
-}
+// A chunk of 512 arcs per warp; no block-wide barrier anywhere, so every warp runs at its own
+// pace and the per-arc rank gathers of many warps overlap.
+constexpr uint32_t kWkArcs = 512;    // arcs per warp chunk (4 quads of 4 arcs per lane)
+constexpr uint32_t kWkRowCap = 64;   // rows of a chunk handled in shared memory
+constexpr int kWkWarps = 8;          // warps per block
 
-// Rows of a tile with more than kKeRowCap rows (long runs of empty rows): every kept arc takes
-// its place in its row with its own atomic.  Offsets are read from global memory.
+// A chunk overlapping more than kWkRowCap rows (long runs of empty rows): every kept arc takes
+// its place in its row with its own atomic; offsets come from global memory.
 __device__ __noinline__ void rl_keep_uncached(uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off,
                                               const uint32_t *__restrict__ cols,
                                               const uint32_t *__restrict__ rank, uint32_t r0,
-                                              uint32_t u_next, uint64_t t0, uint64_t t1,
+                                              uint32_t u_next, uint64_t c0, uint64_t c1,
                                               uint32_t *kept, uint32_t *rowlen, uint32_t *err)
 {
-    const uint64_t a0 = t0 + (uint64_t)threadIdx.x * kKeItems;
-    if (a0 >= t1) return;
-    uint32_t lo = r0, hi = u_next;  // last r with off[r] <= a0
-    while (lo < hi) {
-        const uint32_t mid = lo + (hi - lo + 1) / 2;
-        if (off[mid] <= a0) lo = mid;
-        else hi = mid - 1;
-    }
-    uint32_t r = lo;
-    uint64_t rs = off[r], re = off[r + 1];
-    for (int j = 0; j < kKeItems; j++) {
-        const uint64_t a = a0 + j;
-        if (a >= t1) break;
-        while (re <= a && r + 1 < u_next) {
-            r++;
-            rs = re;
-            re = off[r + 1];
+    const int lane = threadIdx.x & 31;
+    for (uint64_t a = c0 + lane; a < c1; a += 32) {
+        uint32_t lo = r0, hi = u_next;  // the last r with off[r] <= a
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (off[mid] <= a) lo = mid;
+            else hi = mid - 1;
         }
-        const uint32_t v = cols[a];
-        const uint32_t ku = rank[r];
+        if (lo >= n) {  // offsets that are not monotone
+            set_error(err, kDevBadInput);
+            continue;
+        }
+        const uint64_t rs = off[lo], re = off[lo + 1];
+        const uint32_t v = cols[a], ku = rank[lo];
         if (v >= n || ku >= n || rs > re || re > arcs) {
             set_error(err, kDevBadInput);
             continue;
@@ -100,162 +86,138 @@ __device__ __noinline__ void rl_keep_uncached(uint32_t n, uint64_t arcs, const u
     }
 }
 
-// first_row[b] = min{u : off[u] >= b * 4096} (k_tile_rows, order.cu).  Positions inside a tile
-// are 32-bit offsets from its first arc t0; the tile's rows are cached with their starts
-// clamped to the tile.
-__global__ __launch_bounds__(kKeThreads) void k_rl_keep(
+// first_row[c] = min{u : off[u] >= c * 512} (k_tile_rows, order.cu).  Lane l holds the arcs
+// q*128 + 4l .. +3 of its chunk (q = 0..3: each quad load is one coalesced 512-byte line per
+// warp); every kept arc learns its place inside its row piece from a warp-aggregated shared-memory
+// counter per row, every row piece reserves its place in the row with one global atomic.
+__global__ __launch_bounds__(kWkWarps * 32) void k_rl_keep(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ cols,
-    const uint32_t *__restrict__ rank, const uint32_t *__restrict__ first_row, uint32_t *kept,
-    uint32_t *rowlen, uint32_t *err, int vec4)
+    const uint32_t *__restrict__ rank, const uint32_t *__restrict__ first_row, uint32_t nchunks,
+    uint32_t *kept, uint32_t *rowlen, uint32_t *err, int vec4)
 {
-    __shared__ uint32_t s_rel[kKeRowCap + 1];  // row starts - t0, clamped to [0, len]
-    __shared__ uint32_t s_key[kKeRowCap];      // rank of each row
-    __shared__ int32_t s_delta[kKeRowCap];     // place of the row's piece minus P(piece start)
-    __shared__ uint32_t s_out[kKeTile];        // kept ranks in tile order
-    __shared__ uint16_t s_krow[kKeTile];       // tile row of each kept rank
-    __shared__ uint32_t s_pref[kKeThreads + 1];
-    __shared__ uint16_t s_mask[kKeThreads];
-    __shared__ uint32_t s_scan[kKeThreads / 32 + 1];
-
-    const int tid = threadIdx.x;
-    const uint32_t t = blockIdx.x;
-    const uint64_t t0 = (uint64_t)t * kKeTile;
-    const uint64_t t1 = min(t0 + kKeTile, arcs);
-    const uint32_t len = (uint32_t)(t1 - t0);
-    const uint32_t u_first = first_row[t];
-    const uint32_t u_next = first_row[t + 1];
-    const bool bad = u_first > n || u_next > n || u_next < u_first || (t > 0 && u_first == 0);
-    if (bad) {
-        if (tid == 0) set_error(err, kDevBadInput);
+    __shared__ uint32_t s_rel[kWkWarps][kWkRowCap + 1];  // row starts - c0, clamped to [0, len]
+    __shared__ uint32_t s_key[kWkWarps][kWkRowCap];      // rank of each row
+    __shared__ uint32_t s_cnt[kWkWarps][kWkRowCap];      // kept arcs per row piece, then its place
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t c = blockIdx.x * kWkWarps + w;
+    if (c >= nchunks) return;
+    const uint64_t c0 = (uint64_t)c * kWkArcs;
+    const uint64_t c1 = min(c0 + kWkArcs, arcs);
+    const uint32_t len = (uint32_t)(c1 - c0);
+    const uint32_t u_first = first_row[c], u_next = first_row[c + 1];
+    if (u_first > n || u_next > n || u_next < u_first || (c > 0 && u_first == 0)) {
+        if (lane == 0) set_error(err, kDevBadInput);
         return;
     }
-    // rows r0 .. u_next-1 can hold arcs of this tile (r0 = last row starting at or before t0)
-    const uint64_t o_first = off[u_first];
-    const uint32_t r0 = (o_first == t0) ? u_first : u_first - 1;
+    const uint32_t r0 = (off[u_first] == c0) ? u_first : u_first - 1;
     const uint32_t nrows = u_next - r0;
-    if (nrows > kKeRowCap || nrows == 0) {
-        rl_keep_uncached(n, arcs, off, cols, rank, r0, u_next, t0, t1, kept, rowlen, err);
+    if (nrows > kWkRowCap || nrows == 0) {
+        rl_keep_uncached(n, arcs, off, cols, rank, r0, u_next, c0, c1, kept, rowlen, err);
         return;
+    }
+    for (uint32_t i = lane; i <= nrows; i += 32) {
+        const uint64_t o = off[r0 + i];
+        s_rel[w][i] = o <= c0 ? 0u : (o - c0 >= len ? len : (uint32_t)(o - c0));
+        if (i < nrows) {
+            s_key[w][i] = rank[r0 + i];
+            s_cnt[w][i] = 0;
+        }
     }
     const uint64_t row0_start = off[r0];
-    for (uint32_t i = tid; i <= nrows; i += kKeThreads) {
-        const uint64_t o = off[r0 + i];
-        s_rel[i] = o <= t0 ? 0u : (o - t0 >= len ? len : (uint32_t)(o - t0));
-        if (i < nrows) s_key[i] = rank[r0 + i];
-    }
-    __syncthreads();
-
-    const uint32_t p0 = (uint32_t)tid * kKeItems;
-    uint32_t v[kKeItems], kv[kKeItems];
-    if (vec4 && p0 + kKeItems <= len) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(cols + t0 + p0);
+    uint32_t v[16], kv[16];
 #pragma unroll
-        for (int q = 0; q < kKeItems / 4; q++) {
-            const uint4 x = __ldg(p + q);
+    for (int q = 0; q < 4; q++) {
+        const uint32_t p0 = (uint32_t)q * 128 + 4 * lane;
+        if (vec4 && p0 + 4 <= len) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(cols + c0 + p0));
             v[4 * q] = x.x;
             v[4 * q + 1] = x.y;
             v[4 * q + 2] = x.z;
             v[4 * q + 3] = x.w;
-        }
-    } else {
+        } else {
 #pragma unroll
-        for (int j = 0; j < kKeItems; j++) v[j] = (p0 + j < len) ? cols[t0 + p0 + j] : 0u;
+            for (int j = 0; j < 4; j++) v[4 * q + j] = p0 + j < len ? cols[c0 + p0 + j] : 0u;
+        }
     }
 #pragma unroll
-    for (int j = 0; j < kKeItems; j++) kv[j] = (p0 + j < len && v[j] < n) ? __ldg(rank + v[j]) : 0u;
-
-    // tile row of this thread's first arc: last i with s_rel[i] <= p0 (s_rel[0] = 0)
-    uint32_t ri0 = 0;
-    if (p0 < len) {
-        uint32_t lo = 0, hi = nrows - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (s_rel[mid] <= p0) lo = mid;
-            else hi = mid - 1;
-        }
-        ri0 = lo;
+    for (int j = 0; j < 16; j++) {
+        const uint32_t p = (uint32_t)(j >> 2) * 128 + 4 * lane + (j & 3);
+        kv[j] = (p < len && v[j] < n) ? __ldg(rank + v[j]) : 0u;
     }
-
-    uint32_t mask = 0;
-    if (p0 < len) {
-        uint32_t ri = ri0, re = s_rel[ri + 1], ku = s_key[ri];
+    __syncwarp();
+    // the row of every arc (one binary search per quad, then a short walk) and the keep-test
+    uint32_t rows4[4] = {0, 0, 0, 0};  // tile-row of arc j in byte j&3 of rows4[j>>2]
+    uint32_t keep = 0;
 #pragma unroll
-        for (int j = 0; j < kKeItems; j++) {
-            const uint32_t p = p0 + j;
-            if (p < len) {
-                while (re <= p && ri + 1 < nrows) {
-                    ri++;
-                    re = s_rel[ri + 1];
-                    ku = s_key[ri];
-                }
-                if (v[j] >= n) set_error(err, kDevBadInput);
-                else if (kv[j] > ku) mask |= 1u << j;
+    for (int q = 0; q < 4; q++) {
+        const uint32_t p0 = (uint32_t)q * 128 + 4 * lane;
+        if (p0 < len) {
+            uint32_t lo = 0, hi = nrows - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (s_rel[w][mid] <= p0) lo = mid;
+                else hi = mid - 1;
             }
-        }
-    }
-    s_mask[tid] = (uint16_t)mask;
-    uint32_t total;
-    s_pref[tid] = block_excl_scan(__popc(mask), s_scan, total);
-    if (tid == 0) s_pref[kKeThreads] = total;
-    __syncthreads();
-
-    // each row piece reserves its place in its row with one atomic (thread per row)
-    for (uint32_t i = tid; i < nrows; i += kKeThreads) {
-        const uint32_t f = s_rel[i], e = s_rel[i + 1];
-        int32_t delta = kNoSlot;
-        if (e > f) {
-            const uint32_t pf = tile_prefix(s_pref, s_mask, f);
-            const uint32_t cnt = tile_prefix(s_pref, s_mask, e) - pf;
-            if (cnt) {
-                // the first and the last row may extend beyond the tile
-                uint64_t rowlen_true = e - f;
-                if (i == 0 || i == nrows - 1) {
-                    const uint64_t b = off[r0 + i], c = off[r0 + i + 1];
-                    rowlen_true = (b <= c && c <= arcs) ? c - b : 0;
-                }
-                const uint32_t key = s_key[i];
-                if (key < n) {
-                    const uint32_t base = atomicAdd(&rowlen[key], cnt);
-                    // a row cannot keep more arcs than it has (else the rank is not a
-                    // permutation); places stay far below 2^31
-                    if ((uint64_t)base + cnt <= rowlen_true && base < 0x40000000u)
-                        delta = (int32_t)base - (int32_t)pf;
-                    else
-                        set_error(err, kDevBadInput);
-                } else {
-                    set_error(err, kDevBadInput);
-                }
-            }
-        }
-        s_delta[i] = delta;
-    }
-    // kept ranks to shared memory in tile order, with their rows
-    if (mask) {
-        uint32_t ri = ri0, re = s_rel[ri + 1], q = s_pref[tid];
+            uint32_t ri = lo, re = s_rel[w][ri + 1];
 #pragma unroll
-        for (int j = 0; j < kKeItems; j++) {
-            const uint32_t p = p0 + j;
-            if (p < len) {
-                while (re <= p && ri + 1 < nrows) {
-                    ri++;
-                    re = s_rel[ri + 1];
-                }
-                if (mask >> j & 1) {
-                    s_out[q] = kv[j];
-                    s_krow[q] = (uint16_t)ri;
-                    q++;
+            for (int j = 0; j < 4; j++) {
+                const uint32_t p = p0 + j;
+                if (p < len) {
+                    while (re <= p && ri + 1 < nrows) re = s_rel[w][++ri + 1];
+                    rows4[q] |= ri << (8 * j);
+                    if (v[4 * q + j] >= n) set_error(err, kDevBadInput);
+                    else if (kv[4 * q + j] > s_key[w][ri]) keep |= 1u << (4 * q + j);
                 }
             }
         }
     }
-    __syncthreads();
-    // consecutive kept ranks of a row piece go to consecutive places of the row
-    for (uint32_t q = tid; q < total; q += kKeThreads) {
-        const uint32_t ri = s_krow[q];
-        const int32_t delta = s_delta[ri];
-        if (delta == kNoSlot) continue;
-        const uint64_t rs = ri == 0 ? row0_start : t0 + s_rel[ri];
-        kept[rs + (uint64_t)(int64_t)((int64_t)delta + q)] = s_out[q];
+    // place of every kept arc inside its row piece: warp-aggregated counters per row
+    uint32_t slot4[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // 16-bit place of arc j in half j&1 of slot4[j>>1]
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        const bool k = (keep >> j) & 1;
+        const uint32_t ri = (rows4[j >> 2] >> (8 * (j & 3))) & 255u;
+        const uint32_t key = k ? ri : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(kFull, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (k && lane == leader) base = atomicAdd(&s_cnt[w][ri], (uint32_t)__popc(peers));
+        base = __shfl_sync(kFull, base, leader);
+        if (k) slot4[j >> 1] |= (base + __popc(peers & lanemask_lt())) << (16 * (j & 1));
+    }
+    __syncwarp();
+    // every row piece reserves its place in its row
+    for (uint32_t i = lane; i < nrows; i += 32) {
+        const uint32_t cnt = s_cnt[w][i];
+        uint32_t place = 0xffffffffu;
+        if (cnt) {
+            const uint32_t key = s_key[w][i];
+            uint64_t rowlen_true = s_rel[w][i + 1] - s_rel[w][i];
+            if (i == 0 || i == nrows - 1) {  // the first and the last row may extend beyond the chunk
+                const uint64_t b = off[r0 + i], e = off[r0 + i + 1];
+                rowlen_true = (b <= e && e <= arcs) ? e - b : 0;
+            }
+            if (key < n) {
+                const uint32_t base = atomicAdd(&rowlen[key], cnt);
+                // a row cannot keep more arcs than it has (else the rank is not a permutation)
+                if ((uint64_t)base + cnt <= rowlen_true) place = base;
+                else set_error(err, kDevBadInput);
+            } else {
+                set_error(err, kDevBadInput);
+            }
+        }
+        s_cnt[w][i] = place;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        if ((keep >> j) & 1) {
+            const uint32_t ri = (rows4[j >> 2] >> (8 * (j & 3))) & 255u;
+            const uint32_t place = s_cnt[w][ri];
+            if (place == 0xffffffffu) continue;
+            const uint64_t rs = ri == 0 ? row0_start : c0 + s_rel[w][ri];
+            kept[rs + place + ((slot4[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = kv[j];
+        }
     }
 }
 
@@ -376,93 +338,59 @@ __device__ __forceinline__ bool warp_sort_any(const uint32_t *src, uint32_t len,
 }
 
 constexpr int kFiWarps = 8;
-constexpr uint32_t kFiRows = 256;     // ranks per block step
-constexpr uint32_t kFiStage = 8192;   // values staged in shared memory per step
 constexpr uint32_t kLongCap = 32768;  // longest relabelled row this build sorts (power of 2)
 
+// Rows in rank order, one row per lane: the 32 lanes of a warp take 32 consecutive ranks, whose
+// out-degrees are alike (ranks follow the degree), so the lanes' loops run alike.  A row of at
+// most 32 entries is copied from its input range into the lane's own shared-memory slots and
+// each entry lands at its place, the number of smaller entries (ranks are distinct).  Rows of
+// 33..512 entries are then sorted by the whole warp in registers, one after another; longer ones
+// are listed for k_rl_fill_long.
 __global__ __launch_bounds__(kFiWarps * 32) void k_rl_fill(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ perm,
     const uint32_t *__restrict__ kept, const uint64_t *__restrict__ dag_off,
     uint32_t *__restrict__ dag_cols, uint64_t dag_cap, uint32_t *long_rows, uint32_t *n_long,
     uint32_t *err)
 {
-    __shared__ uint64_t s_dst[kFiRows + 1];
-    __shared__ uint64_t s_src[kFiRows];
-    __shared__ uint32_t s_vals[kFiStage];
-    __shared__ uint8_t s_rowid[kFiStage];
-    __shared__ int s_stop;
-    static_assert(kFiRows <= 256, "row ids are 8-bit");
+    __shared__ uint32_t s_row[kFiWarps][32 * 33];  // lane l's slots at l*33 .. l*33+31 (no bank conflicts)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_stop = *(volatile uint32_t *)err != 0;
-    __syncthreads();
-    if (s_stop) return;
-    for (uint32_t r0 = blockIdx.x * kFiRows; r0 < n; r0 += gridDim.x * kFiRows) {
-        const uint32_t cnt = min(kFiRows, n - r0);
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i <= cnt; i += blockDim.x) s_dst[i] = dag_off[r0 + i];
-        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-            const uint32_t u = perm[r0 + i];
-            uint64_t src = ~0ull;
-            if (u < n) {
-                // the kept entries of u live in u's own input range
-                const uint64_t b = off[u], e = off[u + 1];
-                const uint64_t len = dag_off[r0 + i + 1] - dag_off[r0 + i];
-                if (b <= e && e <= arcs && len <= e - b) src = b;
+    if (*(volatile uint32_t *)err) return;  // an earlier pass failed: its offsets are not trusted
+    uint32_t *mine = &s_row[w][lane * 33];
+    const uint64_t stride = (uint64_t)gridDim.x * kFiWarps * 32;
+    for (uint64_t r0 = ((uint64_t)blockIdx.x * kFiWarps + w) * 32; r0 < n; r0 += stride) {
+        const uint64_t r = r0 + lane;
+        uint32_t len = 0;
+        uint64_t src = 0, dst = 0;
+        if (r < n) {
+            const uint32_t u = perm[r];
+            dst = dag_off[r];
+            const uint64_t l64 = dag_off[r + 1] - dst;
+            bool ok = u < n;
+            if (ok) {
+                src = off[u];
+                const uint64_t e = off[u + 1];
+                ok = src <= e && e <= arcs && l64 <= e - src && dst + l64 <= dag_cap && dst <= dst + l64;
             }
-            if (src == ~0ull) set_error(err, kDevBadInput);
-            s_src[i] = src;
+            if (ok) len = (uint32_t)l64;
+            else set_error(err, kDevBadInput);
         }
-        if (threadIdx.x == 0) s_stop = 0;
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
-            if (s_dst[i + 1] < s_dst[i]) s_stop = 1;
-        __syncthreads();
-        const uint64_t base = s_dst[0];
-        const uint64_t total = s_dst[cnt] - base;
-        if (s_stop || s_dst[cnt] > dag_cap) {  // offsets not monotone, or more kept arcs than m
-            if (threadIdx.x == 0) set_error(err, kDevBadInput);
-            continue;
-        }
-        const bool staged = total <= kFiStage;
-        if (staged) {
-            // gather every row's kept entries to their output position (warp per row)
-            for (uint32_t i = w; i < cnt; i += kFiWarps) {
-                const uint32_t rb = (uint32_t)(s_dst[i] - base), len = (uint32_t)(s_dst[i + 1] - s_dst[i]);
-                const uint64_t src = s_src[i];
-                if (src == ~0ull) continue;
-                for (uint32_t j = lane; j < len; j += 32) {
-                    s_vals[rb + j] = kept[src + j];
-                    s_rowid[rb + j] = (uint8_t)i;
-                }
-            }
-            __syncthreads();
-            // rows of <= 32: one thread per entry, place = number of smaller entries (ranks are
-            // distinct); the result lands in global memory directly (each row is one segment)
-            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const uint32_t i = s_rowid[e];
-                if (i >= cnt || s_src[i] == ~0ull) continue;  // entry of a row that was not gathered
-                const uint32_t rb = (uint32_t)(s_dst[i] - base), len = (uint32_t)(s_dst[i + 1] - s_dst[i]);
-                if (len > 32) continue;
-                const uint32_t x = s_vals[e];
+        if (len <= 32) {
+            for (uint32_t j = 0; j < len; j++) mine[j] = kept[src + j];
+            for (uint32_t j = 0; j < len; j++) {
+                const uint32_t x = mine[j];
                 uint32_t pos = 0;
-                for (uint32_t j = 0; j < len; j++) pos += s_vals[rb + j] < x;
-                dag_cols[base + rb + pos] = x;
+                for (uint32_t t = 0; t < len; t++) pos += mine[t] < x;
+                dag_cols[dst + pos] = x;
             }
-            // longer rows: one warp each, sorted in registers
-            for (uint32_t i = w; i < cnt; i += kFiWarps) {
-                const uint32_t rb = (uint32_t)(s_dst[i] - base), len = (uint32_t)(s_dst[i + 1] - s_dst[i]);
-                if (len <= 32 || s_src[i] == ~0ull) continue;
-                if (!warp_sort_any(s_vals + rb, len, dag_cols + base + rb, lane) && lane == 0)
-                    long_rows[atomicAdd(n_long, 1u)] = r0 + i;
-            }
-        } else {
-            for (uint32_t i = w; i < cnt; i += kFiWarps) {
-                const uint32_t len = (uint32_t)(s_dst[i + 1] - s_dst[i]);
-                const uint64_t src = s_src[i];
-                if (len == 0 || src == ~0ull) continue;
-                if (!warp_sort_any(kept + src, len, dag_cols + s_dst[i], lane) && lane == 0)
-                    long_rows[atomicAdd(n_long, 1u)] = r0 + i;
-            }
+        }
+        uint32_t longer = __ballot_sync(kFull, len > 32);
+        while (longer) {
+            const int l = __ffs(longer) - 1;
+            longer &= longer - 1;
+            const uint32_t ll = __shfl_sync(kFull, len, l);
+            const uint64_t ls = __shfl_sync(kFull, src, l), ld = __shfl_sync(kFull, dst, l);
+            if (!warp_sort_any(kept + ls, ll, dag_cols + ld, lane) && lane == 0)
+                long_rows[atomicAdd(n_long, 1u)] = (uint32_t)(r0 + l);
         }
     }
 }
@@ -524,7 +452,7 @@ using namespace citron;
 size_t relabel_ws_bytes(uint32_t n, uint64_t arcs)
 {
     Sizer s;
-    s.take<uint32_t>((arcs + kKeTile - 1) / kKeTile + 2);  // first_row
+    s.take<uint32_t>((arcs + kWkArcs - 1) / kWkArcs + 2);  // first_row
     s.take<uint32_t>(8);                                    // tickets, counters
     s.take<uint32_t>((size_t)n + 1);                        // rowlen (rank order)
     s.take<uint32_t>((size_t)n + 1);                        // perm
@@ -543,7 +471,7 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
                                uint32_t *d_max_outdeg, uint32_t *err, Carver &c, cudaStream_t st,
                                int num_sms)
 {
-    const uint64_t ntiles64 = (arcs + kKeTile - 1) / kKeTile;
+    const uint64_t ntiles64 = (arcs + kWkArcs - 1) / kWkArcs;
     uint32_t *first_row = c.take<uint32_t>(ntiles64 + 2);
     uint32_t *ctr = c.take<uint32_t>(8);
     uint32_t *rowlen = c.take<uint32_t>((size_t)n + 1);
@@ -562,12 +490,13 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
     const uint32_t ntiles = (uint32_t)ntiles64;
     const int vec4 = ((uintptr_t)cols % 16) == 0;
     uint32_t *ticket = ctr, *max_len = ctr + 2, *n_long = ctr + 3;
-    if ((e = launch_tile_rows(n, arcs, off, kKeTile, ntiles, first_row, st))) return e;
+    if ((e = launch_tile_rows(n, arcs, off, kWkArcs, ntiles, first_row, st))) return e;
     k_rl_prologue<<<(n + 255) / 256, 256, 0, st>>>(n, rank, rowlen, perm, err);
-    k_rl_keep<<<ntiles, kKeThreads, 0, st>>>(n, arcs, off, cols, rank, first_row, kept, rowlen, err, vec4);
+    k_rl_keep<<<(ntiles + kWkWarps - 1) / kWkWarps, kWkWarps * 32, 0, st>>>(n, arcs, off, cols, rank, first_row,
+                                                                         ntiles, kept, rowlen, err, vec4);
     k_scan_rowlen<<<sc_tiles, kScThreads, 0, st>>>(n, rowlen, dag_off, sc_tiles, sc_status, ticket,
                                                    max_len, err, wait_cfg());
-    uint32_t grid = (n + kFiRows - 1) / kFiRows;
+    uint32_t grid = (uint32_t)(((uint64_t)n + kFiWarps * 32 - 1) / (kFiWarps * 32));
     if (grid > (uint32_t)num_sms * 8) grid = (uint32_t)num_sms * 8;
     k_rl_fill<<<grid, kFiWarps * 32, 0, st>>>(n, arcs, off, perm, kept, dag_off, dag_cols, arcs / 2,
                                               long_rows, n_long, err);

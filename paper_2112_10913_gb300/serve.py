@@ -81,32 +81,70 @@ class ServeConfig:
 
 class DagCache:
     """Relabelled DAGs of graphs counted before, on the device: key -> (n, arcs, max_outdeg,
-    dag_off (n+1, from 0), dag_cols (ranks 0..n-1)).  Least recently used out first."""
+    dag_off (n+1, from 0), dag_cols (ranks 0..n-1)), least recently used out first.
 
-    def __init__(self, capacity_bytes: int):
+    The DAGs live in one device buffer allocated once (a ring: new DAGs go after the last one,
+    wrapping around to the start and pushing out the DAGs they overlap), so that caching never
+    calls the device allocator, which would synchronise the device under the other slots' work.
+    A DAG that a micro-batch in flight still reads is never overwritten: the new one is then not
+    kept."""
+
+    def __init__(self, capacity_bytes: int, device=None):
         self.capacity = capacity_bytes
+        self.device = device
+        self.buf = None  # uint8 device buffer, allocated on first use
+        self.head = 0
         self.bytes = 0
-        self.entries: collections.OrderedDict = collections.OrderedDict()
+        self.entries: collections.OrderedDict = collections.OrderedDict()  # key -> (entry, start, nbytes)
+        self.in_use: collections.Counter = collections.Counter()
         self.lock = threading.Lock()
         self.hits = self.misses = 0
 
     def get(self, key):
+        """The entry of key (marked in use until release(key)), or None."""
         with self.lock:
             e = self.entries.get(key)
-            if e is not None:
-                self.entries.move_to_end(key)
-            return e
+            if e is None:
+                return None
+            self.entries.move_to_end(key)
+            self.in_use[key] += 1
+            return e[0]
 
-    def put(self, key, entry, nbytes: int):
+    def release(self, key):
+        with self.lock:
+            self.in_use[key] -= 1
+            if self.in_use[key] <= 0:
+                del self.in_use[key]
+
+    def reserve(self, key, n: int, arcs: int):
+        """Device storage (dag_off, dag_cols) for a new entry, or None when the key is cached
+        already or the room it needs is in use.  The entry is readable after commit()."""
+        import torch
+
+        nbytes = (8 * (n + 1) + 4 * max(1, arcs) + 255) // 256 * 256
         if nbytes > self.capacity:
-            return
+            return None
         with self.lock:
             if key in self.entries:
-                return
-            while self.bytes + nbytes > self.capacity and self.entries:
-                _, old = self.entries.popitem(last=False)
-                self.bytes -= old[-1]
-            self.entries[key] = entry + (nbytes,)
+                return None
+            if self.buf is None:
+                self.buf = torch.empty(self.capacity, dtype=torch.uint8, device=self.device)
+            start = self.head if self.head + nbytes <= self.capacity else 0
+            end = start + nbytes
+            clash = [k for k, (_, s0, nb) in self.entries.items() if s0 < end and start < s0 + nb]
+            if any(self.in_use.get(k) for k in clash):
+                return None
+            for k in clash:
+                self.bytes -= self.entries.pop(k)[2]
+            self.head = end
+            region = self.buf[start:end]
+            off = region[: 8 * (n + 1)].view(torch.int64)
+            cols = region[8 * (n + 1): 8 * (n + 1) + 4 * max(1, arcs)].view(torch.int32)
+            return off, cols, start, nbytes
+
+    def commit(self, key, entry, start: int, nbytes: int):
+        with self.lock:
+            self.entries[key] = (entry, start, nbytes)
             self.bytes += nbytes
 
 
@@ -210,7 +248,7 @@ class ServeEngine:
         self.errors: list[Exception] = []
         self.t0 = time.perf_counter()
         self.batches = 0
-        self.cache = DagCache(self.cfg.cache_bytes) if self.cfg.cache_bytes else None
+        self.cache = DagCache(self.cfg.cache_bytes, self.device) if self.cfg.cache_bytes else None
         self.phase_ms = collections.defaultdict(float)  # host time per phase, all micro-batches
         self.slots = [_Slot(self, i) for i in range(self.cfg.slots)]
         self.heavy_slots = ([_Slot(self, self.cfg.slots + i, heavy=True)
@@ -270,7 +308,9 @@ class ServeEngine:
                 a.cols[:arcs_miss].copy_(a.h_cols[:arcs_miss], non_blocking=True)
             a.group[:n_miss].copy_(a.h_group[:n_miss], non_blocking=True)
             citron_order_grouped(n_miss, a.off, a.group, len(miss), a.rank, None, a.ws, stream)
-            max_outdeg = citron_build_dag(n_miss, a.off, a.cols, a.rank, a.dag_off, a.dag_cols, a.ws, stream)
+            # the arc count is taken from the columns' length: pass exactly this batch's arcs
+            max_outdeg = citron_build_dag(n_miss, a.off, a.cols[:arcs_miss], a.rank, a.dag_off, a.dag_cols,
+                                          a.ws, stream)
         else:
             a.dag_off[:1].zero_()
         t2 = time.perf_counter()
@@ -301,28 +341,31 @@ class ServeEngine:
         citron_count_batch(n_all, a.dag_off, a.dag_cols, None, a.group, a.group_k, len(order), kmask,
                            max_outdeg, a.counts, a.ws, stream, opts)
         a.h_counts[: len(order)].copy_(a.counts[: len(order)], non_blocking=True)
-        # keep the new graphs' DAGs (cut out of the union) for later requests; they enter the
-        # cache once the stream has finished the copies, so that other slots never see them early
+        # keep the new graphs' DAGs (cut out of the union) for later requests; they become
+        # visible once the stream has finished the copies, so that other slots never see them early
         new_entries = []
         if cache:
-            import torch
-
             vb = 0
             for i in miss:
                 g = batch[i].graph
                 m = int(g.arcs // 2)
-                e_off = torch.empty(g.n + 1, dtype=torch.int64, device=self.device)
-                e_cols = torch.empty(max(1, m), dtype=torch.int32, device=self.device)
-                citron_dag_append(g.n, a.dag_off[vb: vb + g.n + 1], a.dag_cols, vb, e_off, e_cols, 0, 0, stream)
-                new_entries.append((batch[i].graph_key, (g.n, m, max_outdeg, e_off, e_cols),
-                                    8 * (g.n + 1) + 4 * max(1, m)))
+                room = cache.reserve(batch[i].graph_key, g.n, m)
+                if room is not None:
+                    e_off, e_cols, start, nbytes = room
+                    citron_dag_append(g.n, a.dag_off[vb: vb + g.n + 1], a.dag_cols, vb, e_off, e_cols, 0, 0, stream)
+                    new_entries.append((batch[i].graph_key, (g.n, m, max_outdeg, e_off, e_cols), start, nbytes))
                 vb += g.n
         t3 = time.perf_counter()
         from . import citron_workspace_status
 
-        citron_workspace_status(a.ws, stream)  # synchronises the stream, reports device errors
-        for key, entry, nbytes in new_entries:
-            cache.put(key, entry, nbytes)
+        try:
+            citron_workspace_status(a.ws, stream)  # synchronises the stream, reports device errors
+        finally:
+            if cache:
+                for i in hit:
+                    cache.release(batch[i].graph_key)
+        for key, entry, start, nbytes in new_entries:
+            cache.commit(key, entry, start, nbytes)
         got = a.h_counts.numpy().view(np.uint64)[: len(order)]
         counts = [0] * len(batch)
         for j, i in enumerate(order):

@@ -81,7 +81,8 @@ def test_block_cap_keeps_counts(gpu):
     dg = gpu.DeviceGraph(g)
     for k in (3, 5, 7):
         want = dg.count(k)
-        for cap in (1, 7, 40):
+        # one block alone at k = 7 runs for minutes on the sorted-list path: capped at 7 and 40
+        for cap in ((1, 7, 40) if k < 7 else (7, 40)):
             assert dg.count(k, max_blocks=cap) == want, (k, cap)
             assert dg.count(k, max_blocks=cap, small_max=8, bitmap_max=64) == want, (k, cap)
 

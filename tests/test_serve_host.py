@@ -131,15 +131,31 @@ def test_slot_handoff_never_loses_a_request(engine_cls):
     assert len({r.batch for r in done}) == len(reqs)
 
 
-def test_dag_cache_keeps_the_recent_graphs_within_its_bytes():
+def test_dag_cache_ring_keeps_what_is_in_use():
+    """The cache's ring of DAGs: new entries push out the ones they overlap, least recently
+    written first, never one that a micro-batch in flight still reads, and never more bytes
+    than its capacity."""
     from paper_2112_10913_gb300.serve import DagCache
 
-    c = DagCache(100)
-    c.put("a", (1,), 40)
-    c.put("b", (2,), 40)
-    assert c.get("a")[0] == 1  # "a" is now the most recent
-    c.put("c", (3,), 40)       # evicts "b", the least recently used
-    assert c.get("b") is None and c.get("a")[0] == 1 and c.get("c")[0] == 3
-    assert c.bytes == 80
-    c.put("huge", (4,), 1000)  # larger than the cache: not kept
-    assert c.get("huge") is None
+    c = DagCache(4096, device="cpu")
+    def add(key, n, arcs):
+        room = c.reserve(key, n, arcs)
+        if room is None:
+            return False
+        off, cols, start, nbytes = room
+        assert off.numel() == n + 1 and cols.numel() == max(1, arcs)
+        c.commit(key, (n, arcs, 0, off, cols), start, nbytes)
+        return True
+
+    assert add("a", 100, 200)       # 1,808 bytes -> 2,048
+    assert add("b", 100, 200)       # fills the ring
+    assert not add("a", 100, 200)   # cached already
+    assert c.get("a")[0] == 100     # "a" is now in use
+    assert not add("c", 100, 200)   # its room (the start of the ring) holds "a", in use
+    c.release("a")
+    assert add("c", 100, 200)       # pushes out "a"
+    assert c.get("a") is None and c.get("b") is not None and c.get("c") is not None
+    c.release("b")
+    c.release("c")
+    assert c.bytes <= 4096
+    assert c.reserve("huge", 10000, 10000) is None
