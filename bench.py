@@ -56,10 +56,12 @@ def parse(argv=None):
                    help="wall seconds of sampled oracle counting per k (bands in parallel processes)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="rmat20",
-                   choices=["rmat20", "batch", "serve", "orderings", "list", "chunglu"],
+                   choices=["rmat20", "batch", "serve", "orderings", "list", "chunglu", "count", "order"],
                    help="rmat20: order+count edges/s (default); batch: 4,096-graph batched graphs/s; "
                         "serve: request loop at every rate; orderings: degree vs core ordering; "
-                        "list: clique listing; chunglu: the 4M-vertex power-law graph, k=5..")
+                        "list: clique listing; chunglu: the 4M-vertex power-law graph, k=5..; "
+                        "count: one timed count per k (for profilers); order: the ordering "
+                        "phase's calls timed apart (for profilers)")
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--extras", default="all",
                    help="extra measurements of the default line (N = 1 only), comma list of "
@@ -961,6 +963,76 @@ def run_chunglu(args):
     }
 
 
+def run_count_only(args):
+    """One timed count per k of --ks on R-MAT scale 20, after the DAG is built: the launch a
+    profiler captures for the counting kernels."""
+    from paper_2112_10913_gb300 import build as B
+
+    B.build()
+    import paper_2112_10913_gb300 as cg
+
+    g = workload()
+    G = cg.DeviceGraph(g)
+    per_k = {}
+    for k in [int(x) for x in args.ks.split(",") if x]:
+        for _ in range(max(1, args.steps)):
+            c, o = cg.citron_count_ex(g.n, G.dag_off, G.dag_cols, k, G.ws, G.max_outdeg, time_kernels=True)
+        per_k[str(k)] = dict(count=c, bitmap_kernel_ms=o.kernel_ms[1], small_kernel_ms=o.kernel_ms[0])
+    return {"metric": "counting kernels (one count per k)", "value": None, "unit": "ms",
+            "config": {"workload": "rmat20-ef16", "n": g.n}, "per_k": per_k}
+
+
+def run_order_only(args):
+    """The ordering phase's calls timed apart on R-MAT scale 20 (CUDA events, median of --steps):
+    the degree ordering, the relabelled DAG, Algorithm GenOrdering's DAG."""
+    import torch
+
+    from paper_2112_10913_gb300 import build as B
+
+    B.build()
+    import paper_2112_10913_gb300 as cg
+
+    g = workload()
+    n, arcs = g.n, g.arcs
+    dev = torch.device("cuda")
+    off = torch.from_numpy(g.off.view(np.int64)).to(dev)
+    cols = torch.from_numpy(g.cols.view(np.int32)).to(dev)
+    rank = torch.empty(n, dtype=torch.int32, device=dev)
+    dag_off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    dag_cols = torch.empty(arcs // 2, dtype=torch.int32, device=dev)
+    ws = cg.alloc_workspace(n, arcs, 1024, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        ts = []
+        for i in range(max(1, args.steps)):
+            flush.fill_(i)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res = {
+        "order_ms": timed(lambda: cg.citron_order(n, off, rank, None, ws)),
+        "dag_relabel_ms": timed(lambda: cg.citron_build_dag(n, off, cols, rank, dag_off, dag_cols, ws,
+                                                             want_max_outdeg=False)),
+        "dag_genordering_ms": timed(lambda: cg.citron_build_dag(n, off, cols, None, dag_off, dag_cols, ws,
+                                                                want_max_outdeg=False)),
+    }
+    order_bytes = 8 * (n + 1) + 4 * arcs + 8 * (n + 1) + 4 * (arcs // 2) + 4 * n
+    gen_bytes = 8 * (n + 1) + 4 * arcs + 8 * (n + 1) + 4 * (arcs // 2)
+    t = res["order_ms"] + res["dag_relabel_ms"]
+    return {"metric": "ordering phase (degree ordering + DAG), GB/s of algorithmic bytes",
+            "value": order_bytes / (t / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": t,
+            "frac_of_hbm": order_bytes / (t / 1e3) / 1e9 / _hbm_peak(),
+            "genordering_gb_s": gen_bytes / (res["dag_genordering_ms"] / 1e3) / 1e9,
+            "config": {"workload": "rmat20-ef16", "n": n, "arcs": arcs, "l2": "flushed between reps"},
+            **res}
+
+
 def main():
     args = parse()
     ks = [int(x) for x in args.ks.split(",") if x]
@@ -974,6 +1046,10 @@ def main():
         line = run_list(args)
     elif args.workload == "chunglu":
         line = run_chunglu(args)
+    elif args.workload == "count":
+        line = run_count_only(args)
+    elif args.workload == "order":
+        line = run_order_only(args)
     elif args.impl == "reference":
         line = run_reference(args, ks)
     else:

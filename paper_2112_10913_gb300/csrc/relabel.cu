@@ -18,11 +18,10 @@
 //                   row's out-degree in rank order;
 //   k_scan_rowlen : dag_off = exclusive prefix of rowlen (single pass, decoupled look-back) and
 //                   the largest row;
-//   k_rl_fill     : rows in RANK order, one row per lane: a row of <= 32 entries goes through
-//                   the lane's own shared-memory slots, each entry to its place (the number of
-//                   smaller entries); rows of 33..512 entries are sorted by the whole warp in
-//                   registers (bitonic); longer rows are listed for k_rl_fill_long (one block
-//                   per row).
+//   k_rl_fill     : rows in RANK order, one row per lane: a row of <= 32 entries is sorted by its
+//                   lane in registers (a bitonic network of 4..32 values); rows of 33..512
+//                   entries are sorted by the whole warp in registers (bitonic over the lanes);
+//                   longer rows are listed for k_rl_fill_long (one block per row).
 // The kernels after k_rl_keep return at once when the error word is set: offsets computed
 // after an error are not trusted.
 #include <cuda_runtime.h>
@@ -86,10 +85,11 @@ __device__ __noinline__ void rl_keep_uncached(uint32_t n, uint64_t arcs, const u
     }
 }
 
-// first_row[c] = min{u : off[u] >= c * 512} (k_tile_rows, order.cu).  Lane l holds the arcs
-// q*128 + 4l .. +3 of its chunk (q = 0..3: each quad load is one coalesced 512-byte line per
-// warp); every kept arc learns its place inside its row piece from a warp-aggregated shared-memory
-// counter per row, every row piece reserves its place in the row with one global atomic.
+// first_row[c] = min{u : off[u] >= c * 512} (k_tile_rows, order.cu).  Lane l holds the 16
+// consecutive arcs 16l .. 16l+15 of its chunk.  The place of a kept arc inside its row piece is
+// the number of kept arcs before it in the chunk (a warp prefix over the keep flags) minus that
+// number at the piece's start; every (row, chunk) piece reserves its place in the row with one
+// global atomic.
 __global__ __launch_bounds__(kWkWarps * 32) void k_rl_keep(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ cols,
     const uint32_t *__restrict__ rank, const uint32_t *__restrict__ first_row, uint32_t nchunks,
@@ -97,7 +97,9 @@ __global__ __launch_bounds__(kWkWarps * 32) void k_rl_keep(
 {
     __shared__ uint32_t s_rel[kWkWarps][kWkRowCap + 1];  // row starts - c0, clamped to [0, len]
     __shared__ uint32_t s_key[kWkWarps][kWkRowCap];      // rank of each row
-    __shared__ uint32_t s_cnt[kWkWarps][kWkRowCap];      // kept arcs per row piece, then its place
+    __shared__ int32_t s_place[kWkWarps][kWkRowCap];     // place of the row's piece minus P(start)
+    __shared__ uint32_t s_excl[kWkWarps][33];            // kept arcs before each lane's arcs
+    __shared__ uint16_t s_keep[kWkWarps][32];            // each lane's keep flags
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t c = blockIdx.x * kWkWarps + w;
     if (c >= nchunks) return;
@@ -118,105 +120,106 @@ __global__ __launch_bounds__(kWkWarps * 32) void k_rl_keep(
     for (uint32_t i = lane; i <= nrows; i += 32) {
         const uint64_t o = off[r0 + i];
         s_rel[w][i] = o <= c0 ? 0u : (o - c0 >= len ? len : (uint32_t)(o - c0));
-        if (i < nrows) {
-            s_key[w][i] = rank[r0 + i];
-            s_cnt[w][i] = 0;
-        }
+        if (i < nrows) s_key[w][i] = rank[r0 + i];
     }
     const uint64_t row0_start = off[r0];
+    const uint32_t p0 = 16u * lane;
     uint32_t v[16], kv[16];
+    if (vec4 && p0 + 16 <= len) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(cols + c0 + p0);
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const uint32_t p0 = (uint32_t)q * 128 + 4 * lane;
-        if (vec4 && p0 + 4 <= len) {
-            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(cols + c0 + p0));
+        for (int q = 0; q < 4; q++) {
+            const uint4 x = __ldg(src + q);
             v[4 * q] = x.x;
             v[4 * q + 1] = x.y;
             v[4 * q + 2] = x.z;
             v[4 * q + 3] = x.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; j++) v[4 * q + j] = p0 + j < len ? cols[c0 + p0 + j] : 0u;
         }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = p0 + j < len ? cols[c0 + p0 + j] : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < 16; j++) {
-        const uint32_t p = (uint32_t)(j >> 2) * 128 + 4 * lane + (j & 3);
-        kv[j] = (p < len && v[j] < n) ? __ldg(rank + v[j]) : 0u;
-    }
+    for (int j = 0; j < 16; j++) kv[j] = (p0 + j < len && v[j] < n) ? __ldg(rank + v[j]) : 0u;
     __syncwarp();
-    // the row of every arc (one binary search per quad, then a short walk) and the keep-test
-    uint32_t rows4[4] = {0, 0, 0, 0};  // tile-row of arc j in byte j&3 of rows4[j>>2]
+    // the row of this lane's first arc: the last i with s_rel[i] <= p0
+    uint32_t ri0 = 0;
+    if (p0 < len) {
+        uint32_t lo = 0, hi = nrows - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (s_rel[w][mid] <= p0) lo = mid;
+            else hi = mid - 1;
+        }
+        ri0 = lo;
+    }
     uint32_t keep = 0;
+    if (p0 < len) {
+        uint32_t ri = ri0, re = s_rel[w][ri + 1], ku = s_key[w][ri];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const uint32_t p0 = (uint32_t)q * 128 + 4 * lane;
-        if (p0 < len) {
-            uint32_t lo = 0, hi = nrows - 1;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (s_rel[w][mid] <= p0) lo = mid;
-                else hi = mid - 1;
-            }
-            uint32_t ri = lo, re = s_rel[w][ri + 1];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint32_t p = p0 + j;
-                if (p < len) {
-                    while (re <= p && ri + 1 < nrows) re = s_rel[w][++ri + 1];
-                    rows4[q] |= ri << (8 * j);
-                    if (v[4 * q + j] >= n) set_error(err, kDevBadInput);
-                    else if (kv[4 * q + j] > s_key[w][ri]) keep |= 1u << (4 * q + j);
+        for (int j = 0; j < 16; j++) {
+            const uint32_t p = p0 + j;
+            if (p < len) {
+                while (re <= p && ri + 1 < nrows) {
+                    re = s_rel[w][++ri + 1];
+                    ku = s_key[w][ri];
                 }
+                if (v[j] >= n) set_error(err, kDevBadInput);
+                else if (kv[j] > ku) keep |= 1u << j;
             }
         }
     }
-    // place of every kept arc inside its row piece: warp-aggregated counters per row
-    uint32_t slot4[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // 16-bit place of arc j in half j&1 of slot4[j>>1]
-#pragma unroll
-    for (int j = 0; j < 16; j++) {
-        const bool k = (keep >> j) & 1;
-        const uint32_t ri = (rows4[j >> 2] >> (8 * (j & 3))) & 255u;
-        const uint32_t key = k ? ri : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(kFull, key);
-        const int leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if (k && lane == leader) base = atomicAdd(&s_cnt[w][ri], (uint32_t)__popc(peers));
-        base = __shfl_sync(kFull, base, leader);
-        if (k) slot4[j >> 1] |= (base + __popc(peers & lanemask_lt())) << (16 * (j & 1));
-    }
+    const uint32_t cnt = __popc(keep);
+    const uint32_t incl = warp_incl_scan(cnt);
+    s_excl[w][lane] = incl - cnt;
+    if (lane == 31) s_excl[w][32] = incl;
+    s_keep[w][lane] = (uint16_t)keep;
     __syncwarp();
-    // every row piece reserves its place in its row
+    // P(x): kept arcs of the chunk before position x
+    auto P = [&](uint32_t x) -> uint32_t {
+        const uint32_t q = x >> 4, b = x & 15;
+        return q >= 32 ? s_excl[w][32] : s_excl[w][q] + __popc((uint32_t)s_keep[w][q] & ((1u << b) - 1u));
+    };
     for (uint32_t i = lane; i < nrows; i += 32) {
-        const uint32_t cnt = s_cnt[w][i];
-        uint32_t place = 0xffffffffu;
-        if (cnt) {
+        const uint32_t f = s_rel[w][i], e = s_rel[w][i + 1];
+        int32_t place = INT32_MIN;
+        const uint32_t pf = P(f), k = e > f ? P(e) - pf : 0u;
+        if (k) {
             const uint32_t key = s_key[w][i];
-            uint64_t rowlen_true = s_rel[w][i + 1] - s_rel[w][i];
+            uint64_t rowlen_true = e - f;
             if (i == 0 || i == nrows - 1) {  // the first and the last row may extend beyond the chunk
-                const uint64_t b = off[r0 + i], e = off[r0 + i + 1];
-                rowlen_true = (b <= e && e <= arcs) ? e - b : 0;
+                const uint64_t b = off[r0 + i], t = off[r0 + i + 1];
+                rowlen_true = (b <= t && t <= arcs) ? t - b : 0;
             }
             if (key < n) {
-                const uint32_t base = atomicAdd(&rowlen[key], cnt);
+                const uint32_t base = atomicAdd(&rowlen[key], k);
                 // a row cannot keep more arcs than it has (else the rank is not a permutation)
-                if ((uint64_t)base + cnt <= rowlen_true) place = base;
+                if ((uint64_t)base + k <= rowlen_true && base < 0x40000000u) place = (int32_t)base - (int32_t)pf;
                 else set_error(err, kDevBadInput);
             } else {
                 set_error(err, kDevBadInput);
             }
         }
-        s_cnt[w][i] = place;
+        s_place[w][i] = place;
     }
     __syncwarp();
+    if (keep) {
+        uint32_t ri = ri0, re = s_rel[w][ri + 1];
+        uint32_t q = s_excl[w][lane];
 #pragma unroll
-    for (int j = 0; j < 16; j++) {
-        if ((keep >> j) & 1) {
-            const uint32_t ri = (rows4[j >> 2] >> (8 * (j & 3))) & 255u;
-            const uint32_t place = s_cnt[w][ri];
-            if (place == 0xffffffffu) continue;
-            const uint64_t rs = ri == 0 ? row0_start : c0 + s_rel[w][ri];
-            kept[rs + place + ((slot4[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = kv[j];
+        for (int j = 0; j < 16; j++) {
+            const uint32_t p = p0 + j;
+            if (p < len) {
+                while (re <= p && ri + 1 < nrows) re = s_rel[w][++ri + 1];
+                if ((keep >> j) & 1) {
+                    const int32_t place = s_place[w][ri];
+                    if (place != INT32_MIN) {
+                        const uint64_t rs = ri == 0 ? row0_start : c0 + s_rel[w][ri];
+                        kept[rs + (uint64_t)(int64_t)((int64_t)place + q)] = kv[j];
+                    }
+                    q++;
+                }
+            }
         }
     }
 }
@@ -340,22 +343,57 @@ __device__ __forceinline__ bool warp_sort_any(const uint32_t *src, uint32_t len,
 constexpr int kFiWarps = 8;
 constexpr uint32_t kLongCap = 32768;  // longest relabelled row this build sorts (power of 2)
 
+// Ascending bitonic sorting network over N registers (N a power of two): every index is known at
+// compile time, so the values never leave the registers.
+template <int N>
+__device__ __forceinline__ void net_sort(uint32_t (&v)[N])
+{
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint32_t a = v[i], b = v[l];
+                    const bool up = (i & k) == 0;
+                    v[i] = up ? min(a, b) : max(a, b);
+                    v[l] = up ? max(a, b) : min(a, b);
+                }
+            }
+        }
+    }
+}
+
+// Loads a row of len <= N values (padded with the maximum), sorts it in the thread's registers and
+// stores it.
+template <int N>
+__device__ __forceinline__ void thread_sort_row(const uint32_t *__restrict__ src, uint32_t len,
+                                                uint32_t *__restrict__ dst)
+{
+    uint32_t v[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = (uint32_t)i < len ? src[i] : 0xffffffffu;
+    net_sort<N>(v);
+#pragma unroll
+    for (int i = 0; i < N; i++)
+        if ((uint32_t)i < len) dst[i] = v[i];
+}
+
 // Rows in rank order, one row per lane: the 32 lanes of a warp take 32 consecutive ranks, whose
-// out-degrees are alike (ranks follow the degree), so the lanes' loops run alike.  A row of at
-// most 32 entries is copied from its input range into the lane's own shared-memory slots and
-// each entry lands at its place, the number of smaller entries (ranks are distinct).  Rows of
-// 33..512 entries are then sorted by the whole warp in registers, one after another; longer ones
-// are listed for k_rl_fill_long.
+// out-degrees are alike (ranks follow the degree), so the lanes' work is alike.  A row of at most
+// 32 entries is sorted by its lane alone, in registers (a sorting network of 4, 8, 16 or 32
+// values).  Rows of 33..512 entries are then sorted by the whole warp in registers, one after
+// another; longer ones are listed for k_rl_fill_long.
 __global__ __launch_bounds__(kFiWarps * 32) void k_rl_fill(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ perm,
     const uint32_t *__restrict__ kept, const uint64_t *__restrict__ dag_off,
     uint32_t *__restrict__ dag_cols, uint64_t dag_cap, uint32_t *long_rows, uint32_t *n_long,
     uint32_t *err)
 {
-    __shared__ uint32_t s_row[kFiWarps][32 * 33];  // lane l's slots at l*33 .. l*33+31 (no bank conflicts)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (*(volatile uint32_t *)err) return;  // an earlier pass failed: its offsets are not trusted
-    uint32_t *mine = &s_row[w][lane * 33];
     const uint64_t stride = (uint64_t)gridDim.x * kFiWarps * 32;
     for (uint64_t r0 = ((uint64_t)blockIdx.x * kFiWarps + w) * 32; r0 < n; r0 += stride) {
         const uint64_t r = r0 + lane;
@@ -374,15 +412,13 @@ __global__ __launch_bounds__(kFiWarps * 32) void k_rl_fill(
             if (ok) len = (uint32_t)l64;
             else set_error(err, kDevBadInput);
         }
-        if (len <= 32) {
-            for (uint32_t j = 0; j < len; j++) mine[j] = kept[src + j];
-            for (uint32_t j = 0; j < len; j++) {
-                const uint32_t x = mine[j];
-                uint32_t pos = 0;
-                for (uint32_t t = 0; t < len; t++) pos += mine[t] < x;
-                dag_cols[dst + pos] = x;
-            }
-        }
+        const uint32_t *in = kept + src;
+        uint32_t *out = dag_cols + dst;
+        if (len == 1) out[0] = in[0];
+        else if (len >= 2 && len <= 4) thread_sort_row<4>(in, len, out);
+        else if (len >= 5 && len <= 8) thread_sort_row<8>(in, len, out);
+        else if (len >= 9 && len <= 16) thread_sort_row<16>(in, len, out);
+        else if (len >= 17 && len <= 32) thread_sort_row<32>(in, len, out);
         uint32_t longer = __ballot_sync(kFull, len > 32);
         while (longer) {
             const int l = __ffs(longer) - 1;
@@ -503,8 +539,11 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
     const uint32_t cap_bytes = kLongCap * sizeof(uint32_t);
     if ((e = cudaFuncSetAttribute(k_rl_fill_long, cudaFuncAttributeMaxDynamicSharedMemorySize, cap_bytes)))
         return e;
-    k_rl_fill_long<<<num_sms, 1024, cap_bytes, st>>>(n, arcs, off, perm, kept, dag_off, dag_cols,
-                                                     arcs / 2, long_rows, n_long, kLongCap, err);
+    // rows above 512 are rare in a degree order; a few blocks take them (every block of this
+    // launch holds 128 KB of shared memory, which is costly to set up on every SM)
+    const uint32_t long_grid = num_sms < 16 ? (uint32_t)num_sms : 16u;
+    k_rl_fill_long<<<long_grid, 1024, cap_bytes, st>>>(n, arcs, off, perm, kept, dag_off, dag_cols,
+                                                       arcs / 2, long_rows, n_long, kLongCap, err);
     note_launches(5);
     if (d_max_outdeg)
         if ((e = cudaMemcpyAsync(d_max_outdeg, max_len, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)))
