@@ -6,7 +6,7 @@
 // (Sec. II, Sec. IV) in rank space, where every local subgraph of the counting phase is
 // upper-triangular.
 //
-// Four launches; no block waits on another, and only the scan waits on earlier tiles:
+// Five launches; no block waits on another, and only the scan waits on earlier tiles:
 //   k_rl_prologue : rowlen[r] = 0 and perm[rank[u]] = u (the vertex of each rank);
 //   k_rl_keep     : one pass over the arcs, one chunk of 512 arcs per warp and no block-wide
 //                   barrier.  Per arc u->v the keep-test rank[v] > rank[u] (the 16 rank gathers
@@ -19,9 +19,10 @@
 //   k_scan_rowlen : dag_off = exclusive prefix of rowlen (single pass, decoupled look-back) and
 //                   the largest row;
 //   k_rl_fill     : rows in RANK order, one row per lane: a row of <= 32 entries is sorted by its
-//                   lane in registers (a bitonic network of 4..32 values); rows of 33..512
-//                   entries are sorted by the whole warp in registers (bitonic over the lanes);
-//                   longer rows are listed for k_rl_fill_long (one block per row).
+//                   lane in registers (a bitonic network of 4..32 values); longer rows are listed;
+//   k_rl_fill_mid : one listed row per warp, claimed dynamically: rows of 33..1024 entries are
+//                   sorted by the whole warp in registers (bitonic over the lanes); longer rows
+//                   are listed again for k_rl_fill_long (one block per row).
 // The kernels after k_rl_keep return at once when the error word is set: offsets computed
 // after an error are not trusted.
 #include <cuda_runtime.h>
@@ -328,7 +329,7 @@ __device__ __forceinline__ void warp_sort_row(const uint32_t *src, uint32_t len,
     }
 }
 
-// Sorts a row of 33..512 values with one warp; false when it is longer (left to the long path).
+// Sorts a row of up to 1024 values with one warp; false when it is longer (left to the long path).
 __device__ __forceinline__ bool warp_sort_any(const uint32_t *src, uint32_t len, uint32_t *dst, int lane)
 {
     if (len <= 32) warp_sort_row<1>(src, len, dst, lane);
@@ -336,11 +337,13 @@ __device__ __forceinline__ bool warp_sort_any(const uint32_t *src, uint32_t len,
     else if (len <= 128) warp_sort_row<4>(src, len, dst, lane);
     else if (len <= 256) warp_sort_row<8>(src, len, dst, lane);
     else if (len <= 512) warp_sort_row<16>(src, len, dst, lane);
+    else if (len <= 1024) warp_sort_row<32>(src, len, dst, lane);
     else return false;
     return true;
 }
 
 constexpr int kFiWarps = 8;
+constexpr int kFmWarps = 4;
 constexpr uint32_t kLongCap = 32768;  // longest relabelled row this build sorts (power of 2)
 
 // Ascending bitonic sorting network over N registers (N a power of two): every index is known at
@@ -384,12 +387,12 @@ __device__ __forceinline__ void thread_sort_row(const uint32_t *__restrict__ src
 // Rows in rank order, one row per lane: the 32 lanes of a warp take 32 consecutive ranks, whose
 // out-degrees are alike (ranks follow the degree), so the lanes' work is alike.  A row of at most
 // 32 entries is sorted by its lane alone, in registers (a sorting network of 4, 8, 16 or 32
-// values).  Rows of 33..512 entries are then sorted by the whole warp in registers, one after
-// another; longer ones are listed for k_rl_fill_long.
+// values).  Longer rows are listed (rows[0 .. *n_mid)) for k_rl_fill_mid: in a degree order they
+// sit at the top ranks, and sorting them here would leave those few warps with most of the work.
 __global__ __launch_bounds__(kFiWarps * 32) void k_rl_fill(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ perm,
     const uint32_t *__restrict__ kept, const uint64_t *__restrict__ dag_off,
-    uint32_t *__restrict__ dag_cols, uint64_t dag_cap, uint32_t *long_rows, uint32_t *n_long,
+    uint32_t *__restrict__ dag_cols, uint64_t dag_cap, uint32_t *mid_rows, uint32_t *n_mid,
     uint32_t *err)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -419,19 +422,42 @@ __global__ __launch_bounds__(kFiWarps * 32) void k_rl_fill(
         else if (len >= 5 && len <= 8) thread_sort_row<8>(in, len, out);
         else if (len >= 9 && len <= 16) thread_sort_row<16>(in, len, out);
         else if (len >= 17 && len <= 32) thread_sort_row<32>(in, len, out);
-        uint32_t longer = __ballot_sync(kFull, len > 32);
-        while (longer) {
-            const int l = __ffs(longer) - 1;
-            longer &= longer - 1;
-            const uint32_t ll = __shfl_sync(kFull, len, l);
-            const uint64_t ls = __shfl_sync(kFull, src, l), ld = __shfl_sync(kFull, dst, l);
-            if (!warp_sort_any(kept + ls, ll, dag_cols + ld, lane) && lane == 0)
-                long_rows[atomicAdd(n_long, 1u)] = (uint32_t)(r0 + l);
+        const uint32_t longer = __ballot_sync(kFull, len > 32);
+        if (longer) {
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(n_mid, (uint32_t)__popc(longer));
+            at = __shfl_sync(kFull, at, 0);
+            if (len > 32) mid_rows[at + __popc(longer & lanemask_lt())] = (uint32_t)r;
         }
     }
 }
 
-// One block per listed long row; dynamic shared memory holds the padded row.
+// Rows of 33..1024 entries, one per warp, in the order the warps claim them (one atomic per row;
+// a row's sort costs far more).  Rows above 1024 entries are listed for k_rl_fill_long.
+__global__ __launch_bounds__(kFmWarps * 32, 4) void k_rl_fill_mid(
+    const uint32_t *__restrict__ perm, const uint32_t *__restrict__ kept,
+    const uint64_t *__restrict__ off, const uint64_t *__restrict__ dag_off,
+    uint32_t *__restrict__ dag_cols, const uint32_t *mid_rows, const uint32_t *n_mid, uint32_t *cursor,
+    uint32_t *long_rows, uint32_t *n_long, uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    if (*(volatile uint32_t *)err) return;
+    const uint32_t total = *n_mid;
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(cursor, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= total) break;
+        const uint32_t r = mid_rows[it];
+        // listed by k_rl_fill after its bounds checks: r < n, perm[r] < n, the row fits
+        const uint64_t src = off[perm[r]], dst = dag_off[r];
+        const uint32_t len = (uint32_t)(dag_off[r + 1] - dst);
+        if (!warp_sort_any(kept + src, len, dag_cols + dst, lane) && lane == 0)
+            long_rows[atomicAdd(n_long, 1u)] = r;
+    }
+}
+
+// One block per listed row above 1024 entries; dynamic shared memory holds the padded row.
 __global__ __launch_bounds__(1024) void k_rl_fill_long(
     uint32_t n, uint64_t arcs, const uint64_t *__restrict__ off, const uint32_t *__restrict__ perm,
     const uint32_t *__restrict__ kept, const uint64_t *__restrict__ dag_off,
@@ -493,7 +519,8 @@ size_t relabel_ws_bytes(uint32_t n, uint64_t arcs)
     s.take<uint32_t>((size_t)n + 1);                        // rowlen (rank order)
     s.take<uint32_t>((size_t)n + 1);                        // perm
     s.take<unsigned long long>((size_t)n / kScTile + 2);    // look-back status (scan)
-    s.take<uint32_t>((size_t)n + 1);                        // long rows
+    s.take<uint32_t>((size_t)n + 1);                        // rows above 32 entries
+    s.take<uint32_t>((size_t)n + 1);                        // rows above 1024 entries
     s.take<uint32_t>(arcs + 1);                             // kept ranks, in-row layout
     return s.used;
 }
@@ -514,6 +541,7 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
     uint32_t *perm = c.take<uint32_t>((size_t)n + 1);
     const uint32_t sc_tiles = (n + kScTile - 1) / kScTile;
     unsigned long long *sc_status = c.take<unsigned long long>((size_t)n / kScTile + 2);
+    uint32_t *mid_rows = c.take<uint32_t>((size_t)n + 1);
     uint32_t *long_rows = c.take<uint32_t>((size_t)n + 1);
     uint32_t *kept = c.take<uint32_t>(arcs + 1);
     if (!c.ok) return cudaErrorMemoryAllocation;
@@ -525,7 +553,7 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
         return e;
     const uint32_t ntiles = (uint32_t)ntiles64;
     const int vec4 = ((uintptr_t)cols % 16) == 0;
-    uint32_t *ticket = ctr, *max_len = ctr + 2, *n_long = ctr + 3;
+    uint32_t *ticket = ctr, *max_len = ctr + 2, *n_long = ctr + 3, *n_mid = ctr + 4, *cursor = ctr + 5;
     if ((e = launch_tile_rows(n, arcs, off, kWkArcs, ntiles, first_row, st))) return e;
     k_rl_prologue<<<(n + 255) / 256, 256, 0, st>>>(n, rank, rowlen, perm, err);
     k_rl_keep<<<(ntiles + kWkWarps - 1) / kWkWarps, kWkWarps * 32, 0, st>>>(n, arcs, off, cols, rank, first_row,
@@ -535,16 +563,15 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
     uint32_t grid = (uint32_t)(((uint64_t)n + kFiWarps * 32 - 1) / (kFiWarps * 32));
     if (grid > (uint32_t)num_sms * 8) grid = (uint32_t)num_sms * 8;
     k_rl_fill<<<grid, kFiWarps * 32, 0, st>>>(n, arcs, off, perm, kept, dag_off, dag_cols, arcs / 2,
-                                              long_rows, n_long, err);
+                                              mid_rows, n_mid, err);
+    k_rl_fill_mid<<<(uint32_t)num_sms * 4, kFmWarps * 32, 0, st>>>(perm, kept, off, dag_off, dag_cols, mid_rows,
+                                                                   n_mid, cursor, long_rows, n_long, err);
     const uint32_t cap_bytes = kLongCap * sizeof(uint32_t);
     if ((e = cudaFuncSetAttribute(k_rl_fill_long, cudaFuncAttributeMaxDynamicSharedMemorySize, cap_bytes)))
         return e;
-    // rows above 512 are rare in a degree order; a few blocks take them (every block of this
-    // launch holds 128 KB of shared memory, which is costly to set up on every SM)
-    const uint32_t long_grid = num_sms < 16 ? (uint32_t)num_sms : 16u;
-    k_rl_fill_long<<<long_grid, 1024, cap_bytes, st>>>(n, arcs, off, perm, kept, dag_off, dag_cols,
-                                                       arcs / 2, long_rows, n_long, kLongCap, err);
-    note_launches(5);
+    k_rl_fill_long<<<(uint32_t)num_sms, 1024, cap_bytes, st>>>(n, arcs, off, perm, kept, dag_off, dag_cols,
+                                                               arcs / 2, long_rows, n_long, kLongCap, err);
+    note_launches(6);
     if (d_max_outdeg)
         if ((e = cudaMemcpyAsync(d_max_outdeg, max_len, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)))
             return e;

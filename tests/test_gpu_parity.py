@@ -83,6 +83,18 @@ def test_dag_of_any_rank(gpu, oracle_lib, graphs, which):
     assert G.count(4) == ref
 
 
+def test_relabelled_rows_of_every_sort_length(gpu, oracle_lib):
+    """Rows of every length class of the relabelled fill: sorted by one lane (<= 32 entries), by a
+    warp (33..1024) and by a block (> 1024).  K_1100 in degree order has one row of each length
+    0..1099; a random order of the same graph gives rows of unsorted ranks of every length."""
+    g = gg.complete(1100)
+    for rank in (oracle_lib.degree_rank(g.off, g.n), gg.permutation(7, 7, g.n).argsort().astype(np.uint32)):
+        G = gpu.DeviceGraph(g, rank=rank)
+        off, cols = oracle_lib.dag_by_rank(g.off, g.cols, g.n, rank, relabel=True)
+        dag_equal(G, off, cols)
+        assert G.max_outdeg == 1099
+
+
 PATHS = {
     "default": {},
     "bitmap-only": dict(small_max=1, bitmap_max=1024),
