@@ -141,6 +141,19 @@ struct WarpCtx {
     uint32_t compact3_max; // same for the R = 3 level, which also takes packed 5- and 6-word rows
 };
 
+// Carry-save accumulation of bit counts (a full adder per bit position): the bits of
+// ones + a + b are kept as a new `ones` word and a carry word of weight two (two LOP3s), so that
+// one POPC counts two words.  POPC and the bit scans share the narrow XU pipe, which bounds the
+// leaves; the LOP3s go to the wider ALU pipe.  The running total is s + popc(ones): every user
+// adds popc(ones) once at the end.
+__device__ __forceinline__ void csa_add(uint32_t &ones, uint32_t a, uint32_t b, uint32_t &s)
+{
+    const uint32_t u = ones ^ a;
+    const uint32_t carry = (ones & a) | (u & b);
+    ones = u ^ b;
+    s += 2u * (uint32_t)__popc(carry);
+}
+
 // Number of DAG arcs inside the lane's own candidate set lb (words [lo, hi)): the penultimate
 // level of Counting, which only adds subgraph degrees.  WORK adds the 32-bit word operations
 // (AND + POPC) performed to `work`.
@@ -148,7 +161,7 @@ template <bool WORK>
 __device__ __forceinline__ uint32_t lane_arcs(const WarpCtx &x, const uint32_t *lb, int lo, int hi,
                                               unsigned long long &work)
 {
-    uint32_t s = 0;
+    uint32_t s = 0, ones = 0;
     for (int w = lo; w < hi; w++) {
         uint32_t y = lb[w * 32];
         if (WORK) work += (unsigned long long)__popc(y) * (uint32_t)(hi - (x.tri ? w : lo));
@@ -158,12 +171,11 @@ __device__ __forceinline__ uint32_t lane_arcs(const WarpCtx &x, const uint32_t *
             const uint32_t *rb = x.rows + b * x.RS;
             int w2 = x.tri ? w : lo;
             // two independent word pairs per step keep two shared-memory loads in flight
-            for (; w2 + 1 < hi; w2 += 2)
-                s += __popc(lb[w2 * 32] & rb[w2]) + __popc(lb[w2 * 32 + 32] & rb[w2 + 1]);
+            for (; w2 + 1 < hi; w2 += 2) csa_add(ones, lb[w2 * 32] & rb[w2], lb[w2 * 32 + 32] & rb[w2 + 1], s);
             if (w2 < hi) s += __popc(lb[w2 * 32] & rb[w2]);
         }
     }
-    return s;
+    return s + __popc(ones);
 }
 
 // Writes the candidate set (lane word c) to cbuf and its member indices to elem; returns the
@@ -199,7 +211,7 @@ __device__ __forceinline__ uint32_t tri_rounds(const WarpCtx &x, const uint32_t 
                                                uint32_t total, int hi, int lane,
                                                unsigned long long &work)
 {
-    uint32_t s = 0;
+    uint32_t s = 0, ones = 0;
     const uint32_t lim = (uint32_t)hi << 5;
     for (; j0 < total; j0 += 32) {
         const uint32_t j = j0 + lane;
@@ -213,11 +225,11 @@ __device__ __forceinline__ uint32_t tri_rounds(const WarpCtx &x, const uint32_t 
         int w = (int)(first >> 5);
         for (; w + 1 < hi; w += 2) {
             const uint32_t r0 = in ? rb[w] : 0u, r1 = in ? rb[w + 1] : 0u;
-            s += __popc(cw[w] & r0) + __popc(cw[w + 1] & r1);
+            csa_add(ones, cw[w] & r0, cw[w + 1] & r1, s);
         }
         if (w < hi) s += __popc(cw[w] & (in ? rb[w] : 0u));
     }
-    return s;
+    return s + __popc(ones);
 }
 
 // ---- Compact re-encoding of a small candidate set ------------------------------------------
@@ -392,10 +404,10 @@ __device__ __forceinline__ void build_packed(const WarpCtx &x, uint32_t s, int c
 // Arcs inside the lane's set D (CW words; zero below word Q2) on packed rows; Y = the members
 // to visit (D without its highest member).
 template <int CW, bool WORK, int Q2>
-__device__ __forceinline__ uint32_t packed_leaf(const uint32_t *P, const uint32_t (&D)[CW],
-                                                const uint32_t (&Y)[CW], unsigned long long &work)
+__device__ __forceinline__ void packed_leaf(const uint32_t *P, const uint32_t (&D)[CW],
+                                            const uint32_t (&Y)[CW], uint32_t &ones, uint32_t &s,
+                                            unsigned long long &work)
 {
-    uint32_t s = 0;
     if constexpr (Q2 < CW) {
         uint32_t y = Y[Q2];
         if (WORK) work += (unsigned long long)__popc(y) * (CW - Q2);
@@ -404,11 +416,11 @@ __device__ __forceinline__ uint32_t packed_leaf(const uint32_t *P, const uint32_
             y ^= 1u << jl;
             const uint32_t *rj = P + packed_base<CW>(Q2) + jl * (CW - Q2);
 #pragma unroll
-            for (int w = Q2; w < CW; w++) s += __popc(D[w] & rj[w - Q2]);
+            for (int w = Q2; w + 1 < CW; w += 2) csa_add(ones, D[w] & rj[w - Q2], D[w + 1] & rj[w + 1 - Q2], s);
+            if ((CW - Q2) & 1) s += __popc(D[CW - 1] & rj[CW - 1 - Q2]);
         }
-        s += packed_leaf<CW, WORK, Q2 + 1>(P, D, Y, work);
+        packed_leaf<CW, WORK, Q2 + 1>(P, D, Y, ones, s, work);
     }
-    return s;
 }
 
 // Triangles of a dense compact set of s members (members 0..s-1) on packed rows: lane l takes
@@ -432,7 +444,9 @@ __device__ __forceinline__ void packed_r3(const uint32_t *P, uint32_t s_members,
 #pragma unroll
             for (int w = 0; w < CW; w++) Y[w] = D[w];
             drop_top<CW>(Y);
-            s += packed_leaf<CW, WORK, Q>(P, D, Y, work);
+            uint32_t ones = 0, t = 0;
+            packed_leaf<CW, WORK, Q>(P, D, Y, ones, t, work);
+            s += t + __popc(ones);
         }
         packed_r3<CW, WORK, Q + 1>(P, s_members, lane, s, work);
     }
@@ -450,13 +464,29 @@ __device__ __forceinline__ uint32_t popc_and(const uint32_t (&a)[CW], const uint
     return s;
 }
 
+// popc_and with carry-save pairs: words [FROM, CW) of a & b, two at a time.
+template <int CW, int FROM>
+__device__ __forceinline__ void popc_and_csa(const uint32_t (&a)[CW], const uint4 &b, uint32_t &ones, uint32_t &s)
+{
+    const uint32_t bw[4] = {b.x, b.y, b.z, b.w};
+    int w = FROM;
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        if (w + 1 < CW) {
+            csa_add(ones, a[w] & bw[w], a[w + 1] & bw[w + 1], s);
+            w += 2;
+        }
+    }
+    if (w < CW) s += __popc(a[w] & bw[w]);
+}
+
 // Word q of the members' bits: for R = 2 and 3 lanes take the members of word q (lane l <->
 // member 32q + l).  TRI: compact rows are upper-triangular, so a member's row (and any set
 // derived from it) has no bits in words below the member's own word; those words are skipped
 // at compile time.
 template <int R, int CW, bool TRI, bool WORK, int Q>
 __device__ __forceinline__ void cdfs_word(const uint4 *M, const uint32_t (&C)[CW], int lane,
-                                          uint32_t &s, unsigned long long &work)
+                                          uint32_t &s, uint32_t &ones, unsigned long long &work)
 {
     if constexpr (Q < CW) {
         if ((C[Q] >> lane) & 1) {
@@ -483,16 +513,16 @@ __device__ __forceinline__ void cdfs_word(const uint4 *M, const uint32_t (&C)[CW
                         y ^= 1u << b;
                         const uint32_t j = (uint32_t)(q2 << 5) + b;
                         const uint4 mj = M[j];
-                        if (!TRI) s += popc_and<CW, 0>(D, mj);
-                        else if (q2 == 0) s += popc_and<CW, 0>(D, mj);
-                        else if (q2 == 1) s += popc_and<CW, 1>(D, mj);
-                        else if (q2 == 2) s += popc_and<CW, 2>(D, mj);
-                        else s += popc_and<CW, 3>(D, mj);
+                        if (!TRI) popc_and_csa<CW, 0>(D, mj, ones, s);
+                        else if (q2 == 0) popc_and_csa<CW, 0>(D, mj, ones, s);
+                        else if (q2 == 1) popc_and_csa<CW, 1>(D, mj, ones, s);
+                        else if (q2 == 2) popc_and_csa<CW, 2>(D, mj, ones, s);
+                        else popc_and_csa<CW, 3>(D, mj, ones, s);
                     }
                 }
             }
         }
-        cdfs_word<R, CW, TRI, WORK, Q + 1>(M, C, lane, s, work);
+        cdfs_word<R, CW, TRI, WORK, Q + 1>(M, C, lane, s, ones, work);
     }
 }
 
@@ -512,7 +542,7 @@ __device__ __forceinline__ void cdfs3_dealt(const WarpCtx &x, const uint32_t (&C
         total += __popc(C[q]);
     }
     __syncwarp();
-    uint32_t s = 0;
+    uint32_t s = 0, ones = 0;
     for (uint32_t r0 = 0; r0 < total; r0 += 32) {
         if (r0 + lane < total) {
             const uint32_t m = x.elem[r0 + lane];
@@ -535,16 +565,16 @@ __device__ __forceinline__ void cdfs3_dealt(const WarpCtx &x, const uint32_t (&C
                     y ^= 1u << b;
                     const uint32_t j = (uint32_t)(q2 << 5) + b;
                     const uint4 mj = M[j];
-                    if (!TRI) s += popc_and<CW, 0>(D, mj);
-                    else if (q2 == 0) s += popc_and<CW, 0>(D, mj);
-                    else if (q2 == 1) s += popc_and<CW, 1>(D, mj);
-                    else if (q2 == 2) s += popc_and<CW, 2>(D, mj);
-                    else s += popc_and<CW, 3>(D, mj);
+                    if (!TRI) popc_and_csa<CW, 0>(D, mj, ones, s);
+                    else if (q2 == 0) popc_and_csa<CW, 0>(D, mj, ones, s);
+                    else if (q2 == 1) popc_and_csa<CW, 1>(D, mj, ones, s);
+                    else if (q2 == 2) popc_and_csa<CW, 2>(D, mj, ones, s);
+                    else popc_and_csa<CW, 3>(D, mj, ones, s);
                 }
             }
         }
     }
-    acc += s;
+    acc += s + __popc(ones);
     __syncwarp();
 }
 
@@ -562,9 +592,9 @@ __device__ __forceinline__ void cdfs(const WarpCtx &x, const uint32_t (&C)[CW], 
             acc += t;
         }
     } else if constexpr (R == 2 || R == 3) {
-        uint32_t s = 0;
-        cdfs_word<R, CW, TRI, WORK, 0>(M, C, lane, s, work);
-        acc += s;
+        uint32_t s = 0, ones = 0;
+        cdfs_word<R, CW, TRI, WORK, 0>(M, C, lane, s, ones, work);
+        acc += s + __popc(ones);
     } else {
         // members in order; one recursive call site per level keeps the code linear in R
         uint32_t rem[CW];
