@@ -272,6 +272,20 @@ __device__ __forceinline__ uint32_t compress_with(uint32_t x, uint32_t m, const 
     return x;
 }
 
+// o[q] |= lo, o[q + 1] |= hi for a warp-uniform q (the member prefix of a candidate word is the
+// same on every lane): a uniform branch instead of a select per output word.
+template <int NW>
+__device__ __forceinline__ void place_piece(uint32_t (&o)[NW], uint32_t q, uint32_t lo, uint32_t hi)
+{
+#pragma unroll
+    for (int t = 0; t < NW; t++) {
+        if (q == (uint32_t)t) {
+            o[t] |= lo;
+            if (t + 1 < NW) o[t + 1] |= hi;
+        }
+    }
+}
+
 // Builds the compact rows of the s members of the candidate set (words in cbuf, members in
 // elem, non-zero words [clo, chi)).  NW = 4 output words per row (one uint4) is the width in
 // use; NW = 8 (two uint4 per row) is also supported.
@@ -311,8 +325,7 @@ __device__ __forceinline__ void build_compact(const WarpCtx &x, uint32_t s, int 
             const uint32_t piece = compress_with(row[w], m, mv);
             const uint32_t q = pre >> 5, sh = pre & 31;
             const uint32_t lo = piece << sh, hi = sh ? (piece >> (32 - sh)) : 0u;
-#pragma unroll
-            for (int t = 0; t < NW; t++) o[t] |= (q == (uint32_t)t ? lo : 0u) | (q + 1 == (uint32_t)t ? hi : 0u);
+            place_piece<NW>(o, q, lo, hi);
         }
         if (act) {
             if (NW == 4) {
@@ -389,8 +402,7 @@ __device__ __forceinline__ void build_packed(const WarpCtx &x, uint32_t s, int c
             const uint32_t piece = compress_with(row[w], m, mv);
             const uint32_t qq = pre >> 5, sh = pre & 31;
             const uint32_t lo = piece << sh, hi = sh ? (piece >> (32 - sh)) : 0u;
-#pragma unroll
-            for (int t = 0; t < CW; t++) o[t] |= (qq == (uint32_t)t ? lo : 0u) | (qq + 1 == (uint32_t)t ? hi : 0u);
+            place_piece<CW>(o, qq, lo, hi);
         }
         if (act) {
             uint32_t *dst = x.mbuf + packed_base<CW>(q) + (uint32_t)lane * (CW - q);
