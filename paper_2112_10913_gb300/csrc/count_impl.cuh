@@ -139,6 +139,7 @@ struct WarpCtx {
     uint32_t *mbuf;  // compact rows, 4 words each (16-byte aligned); aliases lbuf
     uint32_t compact_max;  // largest candidate set re-encoded compactly (0 or 128)
     uint32_t compact3_max; // same for the R = 3 level, which also takes packed 5- and 6-word rows
+    uint32_t pair_cap;     // uint16 entries of elem
 };
 
 // Carry-save accumulation of bit counts (a full adder per bit position): the bits of
@@ -644,6 +645,71 @@ __device__ __forceinline__ void cdfs(const WarpCtx &x, const uint32_t (&C)[CW], 
     }
 }
 
+// 4-cliques of a dense compact set of s members (upper-triangular rows M): every arc (i, j) of
+// the set is a pair queued in elem (i << 8 | j), and the queue is worked 32 pairs at a time, lane
+// p forming D = M[i] ∧ M[j] and adding the arcs inside D.  Dealing the members of each C ∧ M[i]
+// on its own leaves the lanes above |C ∧ M[i]| idle; pairs of many i fill every lane.
+template <int CW, bool WORK>
+__device__ __forceinline__ void cdfs4_pairs(const WarpCtx &x, uint32_t s, uint32_t cap, int lane,
+                                            unsigned long long &acc, unsigned long long &work)
+{
+    const uint4 *M = reinterpret_cast<const uint4 *>(x.mbuf);
+    uint16_t *pairs = x.elem;
+    uint32_t sum = 0, ones = 0, n = 0;
+    auto drain = [&]() {
+        __syncwarp();
+        for (uint32_t r0 = 0; r0 < n; r0 += 32) {
+            if (r0 + lane < n) {
+                const uint32_t p = pairs[r0 + lane];
+                const uint4 mi = M[p >> 8], mj = M[p & 255u];
+                uint32_t D[CW];
+                D[0] = mi.x & mj.x;
+                if (CW > 1) D[1] = mi.y & mj.y;
+                if (CW > 2) D[2] = mi.z & mj.z;
+                if (CW > 3) D[3] = mi.w & mj.w;
+                uint32_t Y[CW];
+#pragma unroll
+                for (int w = 0; w < CW; w++) Y[w] = D[w];
+                drop_top<CW>(Y);
+#pragma unroll
+                for (int q2 = 0; q2 < CW; q2++) {
+                    uint32_t y = Y[q2];
+                    if (WORK) work += (unsigned long long)__popc(y) * (CW - q2);
+                    while (y) {
+                        const uint32_t b = 31u - __clz(y);
+                        y ^= 1u << b;
+                        const uint4 mk = M[(uint32_t)(q2 << 5) + b];
+                        if (q2 == 0) popc_and_csa<CW, 0>(D, mk, ones, sum);
+                        else if (q2 == 1) popc_and_csa<CW, 1>(D, mk, ones, sum);
+                        else if (q2 == 2) popc_and_csa<CW, 2>(D, mk, ones, sum);
+                        else popc_and_csa<CW, 3>(D, mk, ones, sum);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        n = 0;
+    };
+    for (uint32_t i = 0; i + 3 < s; i++) {  // a 4-clique needs three members above i
+        if (n + s > cap) drain();
+        const uint4 mi = M[i];
+        const uint32_t w4[4] = {mi.x, mi.y, mi.z, mi.w};
+        if (WORK && lane == 0) work += CW;
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int q = 0; q < CW; q++) cnt += __popc(w4[q]);
+        if (cnt < 3) continue;  // prune: fewer than three members above i
+#pragma unroll
+        for (int q = 0; q < CW; q++) {
+            const uint32_t m = w4[q];
+            if ((m >> lane) & 1) pairs[n + __popc(m & lanemask_lt())] = (uint16_t)((i << 8) | (uint32_t)(q * 32 + lane));
+            n += __popc(m);
+        }
+    }
+    drain();
+    acc += sum + __popc(ones);
+}
+
 template <int R, int CW, bool TRI, bool WORK>
 __device__ __forceinline__ void cdfs_all(const WarpCtx &x, uint32_t s, int lane,
                                          unsigned long long &acc, unsigned long long &work)
@@ -654,7 +720,8 @@ __device__ __forceinline__ void cdfs_all(const WarpCtx &x, uint32_t s, int lane,
         const uint32_t lo = q * 32;
         C[q] = s >= lo + 32 ? kFull : (s > lo ? ((1u << (s - lo)) - 1) : 0u);
     }
-    cdfs<R, CW, TRI, WORK>(x, C, lane, acc, work);
+    if constexpr (R == 4 && TRI) cdfs4_pairs<CW, WORK>(x, s, x.pair_cap, lane, acc, work);
+    else cdfs<R, CW, TRI, WORK>(x, C, lane, acc, work);
 }
 
 // Entry for a candidate set of at most compact_max members (lane word c), triangular layout.
@@ -888,6 +955,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     x.mbuf = x.lbuf;
     x.compact_max = compact_max;
     x.compact3_max = compact_max ? 192u : 0u;
+    x.pair_cap = dcap;
     const uint32_t nlist = st->n_mid;
     if (block_ns && threadIdx.x == 0) block_ns[2 * blockIdx.x] = global_ns();
     unsigned long long block_total = 0;  // meaningful in thread 0
