@@ -424,10 +424,19 @@ __device__ __forceinline__ void packed_leaf(const uint32_t *P, const uint32_t (&
     if constexpr (Q2 < CW) {
         uint32_t y = Y[Q2];
         if (WORK) work += (unsigned long long)__popc(y) * (CW - Q2);
-        while (y) {
-            const uint32_t jl = 31u - __clz(y);
-            y ^= 1u << jl;
-            const uint32_t *rj = P + packed_base<CW>(Q2) + jl * (CW - Q2);
+        // two members per step (the highest and the lowest), their words paired in the adder
+        while (y & (y - 1u)) {
+            const uint32_t j1 = 31u - __clz(y);
+            const uint32_t lb = y & (0u - y);
+            const uint32_t j2 = 31u - __clz(lb);
+            y ^= (1u << j1) | lb;
+            const uint32_t *r1 = P + packed_base<CW>(Q2) + j1 * (CW - Q2);
+            const uint32_t *r2 = P + packed_base<CW>(Q2) + j2 * (CW - Q2);
+#pragma unroll
+            for (int w = Q2; w < CW; w++) csa_add(ones, D[w] & r1[w - Q2], D[w] & r2[w - Q2], s);
+        }
+        if (y) {
+            const uint32_t *rj = P + packed_base<CW>(Q2) + (31u - __clz(y)) * (CW - Q2);
 #pragma unroll
             for (int w = Q2; w + 1 < CW; w += 2) csa_add(ones, D[w] & rj[w - Q2], D[w + 1] & rj[w + 1 - Q2], s);
             if ((CW - Q2) & 1) s += __popc(D[CW - 1] & rj[CW - 1 - Q2]);
@@ -493,6 +502,45 @@ __device__ __forceinline__ void popc_and_csa(const uint32_t (&a)[CW], const uint
     if (w < CW) s += __popc(a[w] & bw[w]);
 }
 
+// Two leaf members at once: words [FROM, CW) of D & b1 and of D & b2 paired in the carry-save
+// adder (one POPC per word pair).
+template <int CW, int FROM>
+__device__ __forceinline__ void popc_and_csa2(const uint32_t (&a)[CW], const uint4 &b1, const uint4 &b2,
+                                              uint32_t &ones, uint32_t &s)
+{
+    const uint32_t v1[4] = {b1.x, b1.y, b1.z, b1.w}, v2[4] = {b2.x, b2.y, b2.z, b2.w};
+#pragma unroll
+    for (int w = FROM; w < CW; w++) csa_add(ones, a[w] & v1[w], a[w] & v2[w], s);
+}
+
+// Arcs from the members y of word q2 (FROM = q2 on triangular rows, else 0) into D, on compact
+// rows M: two members per step, the highest and the lowest, whose bit scans and row loads are
+// independent of each other.
+template <int CW, int FROM>
+__device__ __forceinline__ void leaf_word(const uint4 *M, const uint32_t (&D)[CW], uint32_t y, uint32_t base,
+                                          uint32_t &ones, uint32_t &s)
+{
+    while (y & (y - 1u)) {
+        const uint32_t b1 = 31u - __clz(y);
+        const uint32_t lb = y & (0u - y);
+        const uint32_t b2 = 31u - __clz(lb);
+        y ^= (1u << b1) | lb;
+        popc_and_csa2<CW, FROM>(D, M[base + b1], M[base + b2], ones, s);
+    }
+    if (y) popc_and_csa<CW, FROM>(D, M[base + 31u - __clz(y)], ones, s);
+}
+
+template <int CW, bool TRI>
+__device__ __forceinline__ void leaf_word_any(const uint4 *M, const uint32_t (&D)[CW], uint32_t y, int q2,
+                                              uint32_t &ones, uint32_t &s)
+{
+    const uint32_t base = (uint32_t)q2 << 5;
+    if (!TRI || q2 == 0) leaf_word<CW, 0>(M, D, y, base, ones, s);
+    else if (q2 == 1) leaf_word<CW, (CW > 1 ? 1 : 0)>(M, D, y, base, ones, s);
+    else if (q2 == 2) leaf_word<CW, (CW > 2 ? 2 : 0)>(M, D, y, base, ones, s);
+    else leaf_word<CW, (CW > 3 ? 3 : 0)>(M, D, y, base, ones, s);
+}
+
 // Word q of the members' bits: for R = 2 and 3 lanes take the members of word q (lane l <->
 // member 32q + l).  TRI: compact rows are upper-triangular, so a member's row (and any set
 // derived from it) has no bits in words below the member's own word; those words are skipped
@@ -521,17 +569,7 @@ __device__ __forceinline__ void cdfs_word(const uint4 *M, const uint32_t (&C)[CW
                 for (int q2 = TRI ? Q : 0; q2 < CW; q2++) {
                     uint32_t y = Y[q2];
                     if (WORK) work += (unsigned long long)__popc(y) * (TRI ? CW - q2 : CW);
-                    while (y) {
-                        const uint32_t b = 31u - __clz(y);
-                        y ^= 1u << b;
-                        const uint32_t j = (uint32_t)(q2 << 5) + b;
-                        const uint4 mj = M[j];
-                        if (!TRI) popc_and_csa<CW, 0>(D, mj, ones, s);
-                        else if (q2 == 0) popc_and_csa<CW, 0>(D, mj, ones, s);
-                        else if (q2 == 1) popc_and_csa<CW, 1>(D, mj, ones, s);
-                        else if (q2 == 2) popc_and_csa<CW, 2>(D, mj, ones, s);
-                        else popc_and_csa<CW, 3>(D, mj, ones, s);
-                    }
+                    leaf_word_any<CW, TRI>(M, D, y, q2, ones, s);
                 }
             }
         }
@@ -573,17 +611,7 @@ __device__ __forceinline__ void cdfs3_dealt(const WarpCtx &x, const uint32_t (&C
             for (int q2 = 0; q2 < CW; q2++) {
                 uint32_t y = Y[q2];  // zero below the member's own word when TRI
                 if (WORK) work += (unsigned long long)__popc(y) * (TRI ? CW - q2 : CW);
-                while (y) {
-                    const uint32_t b = 31u - __clz(y);
-                    y ^= 1u << b;
-                    const uint32_t j = (uint32_t)(q2 << 5) + b;
-                    const uint4 mj = M[j];
-                    if (!TRI) popc_and_csa<CW, 0>(D, mj, ones, s);
-                    else if (q2 == 0) popc_and_csa<CW, 0>(D, mj, ones, s);
-                    else if (q2 == 1) popc_and_csa<CW, 1>(D, mj, ones, s);
-                    else if (q2 == 2) popc_and_csa<CW, 2>(D, mj, ones, s);
-                    else popc_and_csa<CW, 3>(D, mj, ones, s);
-                }
+                leaf_word_any<CW, TRI>(M, D, y, q2, ones, s);
             }
         }
     }
@@ -675,15 +703,7 @@ __device__ __forceinline__ void cdfs4_pairs(const WarpCtx &x, uint32_t s, uint32
                 for (int q2 = 0; q2 < CW; q2++) {
                     uint32_t y = Y[q2];
                     if (WORK) work += (unsigned long long)__popc(y) * (CW - q2);
-                    while (y) {
-                        const uint32_t b = 31u - __clz(y);
-                        y ^= 1u << b;
-                        const uint4 mk = M[(uint32_t)(q2 << 5) + b];
-                        if (q2 == 0) popc_and_csa<CW, 0>(D, mk, ones, sum);
-                        else if (q2 == 1) popc_and_csa<CW, 1>(D, mk, ones, sum);
-                        else if (q2 == 2) popc_and_csa<CW, 2>(D, mk, ones, sum);
-                        else popc_and_csa<CW, 3>(D, mk, ones, sum);
-                    }
+                    leaf_word_any<CW, true>(M, D, y, q2, ones, sum);
                 }
             }
         }
