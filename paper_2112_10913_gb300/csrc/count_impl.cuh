@@ -166,12 +166,23 @@ __device__ __forceinline__ uint32_t lane_arcs(const WarpCtx &x, const uint32_t *
     for (int w = lo; w < hi; w++) {
         uint32_t y = lb[w * 32];
         if (WORK) work += (unsigned long long)__popc(y) * (uint32_t)(hi - (x.tri ? w : lo));
-        while (y) {
-            const uint32_t b = (uint32_t)(w << 5) + __ffs(y) - 1;
-            y &= y - 1;
+        // two members per step (the highest and the lowest bit): independent scans and loads
+        while (y & (y - 1u)) {
+            const uint32_t b1 = 31u - __clz(y);
+            const uint32_t lbit = y & (0u - y);
+            const uint32_t b2 = 31u - __clz(lbit);
+            y ^= (1u << b1) | lbit;
+            const uint32_t *r1 = x.rows + ((uint32_t)(w << 5) + b1) * x.RS;
+            const uint32_t *r2 = x.rows + ((uint32_t)(w << 5) + b2) * x.RS;
+            for (int w2 = x.tri ? w : lo; w2 < hi; w2++) {
+                const uint32_t l = lb[w2 * 32];
+                csa_add(ones, l & r1[w2], l & r2[w2], s);
+            }
+        }
+        if (y) {
+            const uint32_t b = (uint32_t)(w << 5) + 31u - __clz(y);
             const uint32_t *rb = x.rows + b * x.RS;
             int w2 = x.tri ? w : lo;
-            // two independent word pairs per step keep two shared-memory loads in flight
             for (; w2 + 1 < hi; w2 += 2) csa_add(ones, lb[w2 * 32] & rb[w2], lb[w2 * 32 + 32] & rb[w2 + 1], s);
             if (w2 < hi) s += __popc(lb[w2 * 32] & rb[w2]);
         }
