@@ -110,7 +110,7 @@ def workload():
 
 
 # ---------------------------------------------------------------------------------------------
-# CPU side: the oracle (whole jobs where it finishes, else a stratified sample of roots)
+# CPU side: the oracle (whole jobs where it finishes, else a stratified sample of edge tasks)
 
 BANDS = [(0, 8), (8, 16), (16, 32), (32, 64), (64, 128), (128, 256), (256, 512), (512, 1 << 30)]
 
@@ -126,37 +126,46 @@ def oracle_order(g):
 
 
 def _band_worker(dag_off, dag_cols, n, k, plan, q):
-    """Runs in a spawned process: for every out-degree band in turn (lightest first), times the
-    oracle's count on one thread for each group of the band's sampled roots, and reports each
-    group as soon as it is done."""
+    """Runs in a spawned process: times the oracle's edge tasks on one thread, one group of
+    sampled DAG arcs at a time in the plan's order, and reports each group as soon as it is
+    done."""
     import oracle
 
     oracle.build()
-    # the cost of a call that counts nothing (thread start, scratch set-up): subtracted per group
-    idle = np.array([int(np.argmin(np.diff(dag_off)))], dtype=np.uint32)
+    # the cost of a call that counts nothing (row-width scan, scratch set-up): subtracted per group
+    none = np.zeros(0, dtype=np.uint64)
     cost = []
     for _ in range(7):
         t0 = time.perf_counter()
-        oracle.count_roots(dag_off, dag_cols, n, k, idle, 1)
+        oracle.count_arcs(dag_off, dag_cols, n, k, none)
         cost.append(time.perf_counter() - t0)
     q.put(("call", 0, float(np.median(cost))))
-    for band, chunks in plan:
-        for ch in chunks:
-            t0 = time.perf_counter()
-            oracle.count_roots(dag_off, dag_cols, n, k, ch, 1)
-            q.put((band, int(ch.size), time.perf_counter() - t0))
+    for band, arcs in plan:
+        t0 = time.perf_counter()
+        oracle.count_arcs(dag_off, dag_cols, n, k, arcs)
+        q.put((band, int(arcs.size), time.perf_counter() - t0))
     q.put(None)
 
 
-def oracle_stratified(dag, n, k, budget_s, seed=2, groups=4, per=16):
-    """Single-thread oracle counting time of one k, estimated from a stratified sample of roots.
-    The roots that can hold a k-clique are split into out-degree bands; every band gets `groups`
-    seeded groups of `per` roots, timed on one thread (one worker process, bands from the
-    lightest up); a band's time is its size times its mean time per sampled root
-    (inverse-probability weighting), with a standard error from the spread of its groups.
-    Sampling stops at budget_s (the worker is stopped): a band with no group done by then is left
-    out, and the estimate is then a lower bound.  Returns (seconds on one thread, standard error,
-    sampled roots, bands left out)."""
+def _group_size(lo: int) -> int:
+    """Arcs per timed group in a band whose roots have out-degree above lo: many cheap edge tasks
+    per call in light bands (so the call's own cost stays small against them), few in heavy
+    ones (an edge task of a heavy root can take a tenth of a second at k = 6)."""
+    return max(4, min(256, 4096 // max(lo, 16)))
+
+
+def oracle_stratified(dag, n, k, budget_s, seed=2, groups=8, per=None):
+    """Single-thread oracle counting time of one k (k >= 3), estimated from a stratified sample
+    of edge tasks.  The unit is the edge-parallel form's task: the k-cliques whose first two
+    vertices are the ends of one DAG arc (the oracle's count_arcs; a root's time is the sum of
+    its arcs' times).  Arcs of the roots that can hold a k-clique are split into bands by their
+    root's out-degree; every band gets up to `groups` seeded groups of arcs (per arcs each, else
+    a size set by the band), timed on one thread in one worker process, round-robin over the
+    bands from the heaviest down, so that every band is sampled early.  A band's time is its arc
+    count times its mean time per sampled arc (inverse-probability weighting), with a standard
+    error from the spread of its groups.  Sampling stops at budget_s (the worker is stopped): a
+    band with no group done by then is left out, and the estimate is then a lower bound.
+    Returns (seconds on one thread, standard error, sampled arcs, bands left out)."""
     import multiprocessing as mp
     import queue as queue_mod
 
@@ -164,15 +173,27 @@ def oracle_stratified(dag, n, k, budget_s, seed=2, groups=4, per=16):
 
     dag_off, dag_cols = dag
     outdeg = np.diff(dag_off).astype(np.int64)
-    plan, sizes, takes = [], {}, {}
+    chunks, sizes, takes = {}, {}, {}
     for b, (lo, hi) in enumerate(BANDS):
-        ids = np.nonzero((outdeg >= max(k - 1, lo + 1)) & (outdeg <= hi))[0]
-        if not ids.size:
+        roots = np.nonzero((outdeg >= max(k - 1, lo + 1)) & (outdeg <= hi))[0]
+        if not roots.size:
             continue
-        ids = ids[gg.permutation(seed, 20 + b, ids.size)]
-        take = min(ids.size, per * groups)
-        plan.append((b, [c.astype(np.uint32) for c in np.array_split(ids[:take], min(groups, take)) if c.size]))
-        sizes[b], takes[b] = int(ids.size), take
+        starts = dag_off[roots].astype(np.int64)
+        lens = outdeg[roots]
+        total = int(lens.sum())
+        # every arc of the band's roots, then a seeded sample of them
+        ids = np.repeat(starts - np.concatenate(([0], np.cumsum(lens)[:-1])), lens) + np.arange(total)
+        ids = ids[gg.permutation(seed, 20 + b, total)]
+        gsize = per if per is not None else _group_size(lo)
+        take = min(total, gsize * groups)
+        nch = max(1, -(-take // gsize))
+        chunks[b] = [c.astype(np.uint64) for c in np.array_split(ids[:take], nch) if c.size]
+        sizes[b], takes[b] = total, take
+    plan = []
+    for r in range(max((len(c) for c in chunks.values()), default=0)):
+        for b in sorted(chunks, reverse=True):
+            if r < len(chunks[b]):
+                plan.append((b, chunks[b][r]))
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     proc = ctx.Process(target=_band_worker, args=(dag_off, dag_cols, n, k, plan, q), daemon=True)
@@ -210,9 +231,9 @@ def oracle_stratified(dag, n, k, budget_s, seed=2, groups=4, per=16):
 def cpu_baseline_obj(g, ks, budget_s, gpu_counts=None):
     """The oracle on this host's cores for the same jobs: ordering + DAG on the whole graph;
     counting on the whole graph, all threads, for k <= 4 (checked against the GPU's count); for
-    larger k, the single-thread time estimated from a stratified root sample (oracle_stratified)
-    over the thread count (the oracle's roots are independent tasks taken dynamically: ideal
-    scaling is assumed)."""
+    larger k, the single-thread time estimated from a stratified sample of edge tasks
+    (oracle_stratified) over the thread count (the oracle's roots are independent tasks taken
+    dynamically: ideal scaling is assumed)."""
     import oracle
 
     oracle.build()
@@ -236,13 +257,15 @@ def cpu_baseline_obj(g, ks, budget_s, gpu_counts=None):
             scale = 1.0 / threads
             est, se = t1 * scale, se1 * scale
             per_k[str(k)] = dict(seconds=t_order + est, order_s=t_order, count_s=est, count_se_s=se,
-                                 single_thread_s=t1, sample=f"{m} roots stratified by out-degree",
+                                 single_thread_s=t1,
+                                 sample=f"{m} edge tasks (DAG arcs) stratified by their root's out-degree",
                                  bands_not_sampled=[list(b) for b in missing],
                                  lower_bound=bool(missing))
             total += t_order + est
             se2 += se * se
             lower = lower or bool(missing)
-            samples.append(f"k={k} from {m} roots stratified by out-degree, single-thread times "
+            samples.append(f"k={k} from {m} edge tasks (DAG arcs) stratified by their root's out-degree, "
+                           "single-thread times "
                            "weighted by inverse sampling probability, over the thread count"
                            + (f" (out-degree bands {missing} not sampled within {budget_s:.0f} s: "
                               "a lower bound on the time)" if missing else ""))
@@ -708,8 +731,9 @@ def run_reference(args, ks):
     t = statistics.mean(times)
     value = g.m * len(ks) / t
     sample = (f"oracle ordering + DAG on the whole graph per job; counting time per k estimated from "
-              f"roots stratified by out-degree ({budget:.1f} s of single-thread sampling per k, "
-              f"inverse-probability weighted, divided by {threads} threads; last k: {last} roots)")
+              f"edge tasks (DAG arcs) stratified by their root's out-degree ({budget:.1f} s of "
+              f"single-thread sampling per k, inverse-probability weighted, divided by {threads} "
+              f"threads; last k: {last} arcs)")
     return {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

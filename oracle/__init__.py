@@ -74,6 +74,8 @@ def lib():
         L.oracle_count_roots.restype = i32
         L.oracle_count_per_edge.argtypes = [u32, p, p, i32, p]
         L.oracle_count_per_edge.restype = i32
+        L.oracle_count_arcs.argtypes = [u32, p, p, i32, p, u64, p, p]
+        L.oracle_count_arcs.restype = i32
         _lib = L
     return _lib
 
@@ -178,6 +180,17 @@ def count_per_edge(dag_off, dag_cols, n: int, k: int) -> np.ndarray:
     out = np.zeros(max(1, dag_cols.size), dtype=np.uint64)
     _check(lib().oracle_count_per_edge(n, _ptr(dag_off), _ptr(dag_cols), k, _ptr(out)))
     return out[: dag_cols.size]
+
+
+def count_arcs(dag_off, dag_cols, n: int, k: int, arcs, per_arc: bool = False):
+    """Edge tasks of the listed DAG arc indices (k >= 3), on one thread: their total and, with
+    per_arc, the count of each (the entries of count_per_edge at those arcs)."""
+    dag_off, dag_cols, arcs = _c(dag_off, np.uint64), _c(dag_cols, np.uint32), _c(arcs, np.uint64)
+    out = np.zeros(1, dtype=np.uint64)
+    pa = np.zeros(max(1, arcs.size), dtype=np.uint64)
+    _check(lib().oracle_count_arcs(n, _ptr(dag_off), _ptr(dag_cols), k, _ptr(arcs), arcs.size, _ptr(pa),
+                                   _ptr(out)))
+    return (int(out[0]), pa[: arcs.size]) if per_arc else int(out[0])
 
 
 def count_graph(g, k: int, threads: int | None = None) -> int:

@@ -496,3 +496,54 @@ int oracle_count_per_edge(uint32_t n, const uint64_t *dag_off, const uint32_t *d
     free(levels);
     return st;
 }
+
+/* The same edge-level form for a listed subset of arcs: per_arc[i] = the number of k-cliques
+ * whose first two vertices in the DAG order are the ends (u, v) of DAG arc arcs[i] (k >= 3), and
+ * *out their sum.  The row u owning an arc index is found by binary search in dag_off.  One
+ * thread; used to time a sample of edge tasks (the units of the edge-parallel form). */
+int oracle_count_arcs(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_adj, int k,
+                      const uint64_t *arcs, uint64_t narcs, uint64_t *per_arc, uint64_t *out)
+{
+    *out = 0;
+    if (k < 3) return ORACLE_E_ARG;
+    dag_t g = {n, dag_off, dag_adj};
+    uint32_t width = max_row(&g);
+    int depth = k - 2;
+    uint32_t *store = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)width + 1) * (depth + 1));
+    uint32_t **levels = (uint32_t **)malloc(sizeof(uint32_t *) * (size_t)(depth + 1));
+    if (!store || !levels) {
+        free(store);
+        free(levels);
+        return ORACLE_E_NOMEM;
+    }
+    for (int i = 0; i <= depth; i++) levels[i] = store + (size_t)i * (width + 1);
+    int st = ORACLE_OK;
+    uint64_t total = 0;
+    for (uint64_t i = 0; i < narcs && !st; i++) {
+        uint64_t e = arcs[i];
+        if (e >= dag_off[n]) {
+            st = ORACLE_E_ARG;
+            break;
+        }
+        /* u = the last row with dag_off[u] <= e (rows may be empty) */
+        uint32_t lo = 0, hi = n - 1;
+        while (lo < hi) {
+            uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (dag_off[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        uint32_t u = lo, v = dag_adj[e];
+        const uint32_t *nu = dag_adj + dag_off[u];
+        uint32_t du = (uint32_t)(dag_off[u + 1] - dag_off[u]);
+        uint32_t len = intersect(nu, du, dag_adj + dag_off[v], dag_off[v + 1] - dag_off[v], levels[0]);
+        uint64_t c;
+        st = cnt(&g, levels[0], len, k - 2, levels + 1, &c);
+        if (st) break;
+        if (per_arc) per_arc[i] = c;
+        if (__builtin_add_overflow(total, c, &total)) st = ORACLE_E_OVERFLOW;
+    }
+    *out = total;
+    free(store);
+    free(levels);
+    return st;
+}

@@ -1,5 +1,6 @@
-"""Host logic of bench.py, on the CPU: the extras switch and the oracle's stratified root sample
-(the CPU baseline's estimator), whose bands cover every root that can hold a k-clique."""
+"""Host logic of bench.py, on the CPU: the extras switch and the oracle's stratified sample of
+edge tasks (the CPU baseline's estimator), whose bands cover every arc of the roots that can hold
+a k-clique."""
 import numpy as np
 
 import bench
@@ -18,8 +19,11 @@ def test_stratified_sample_covers_the_eligible_roots(oracle_lib):
     dag, _ = bench.oracle_order(g)
     outdeg = np.diff(dag[0])
     for k in (4, 5):
-        eligible = int((outdeg >= k - 1).sum())
+        eligible = int(outdeg[outdeg >= k - 1].sum())
         # groups as large as the bands, within a generous budget: every band is sampled completely
         est, se, sampled, missing = bench.oracle_stratified(dag, g.n, k, budget_s=120, per=10 ** 6)
         assert sampled == eligible and not missing
         assert est >= 0.0 and se == 0.0  # a tiny graph may cost no more than the calls themselves
+        # the default plan: every band sampled, round-robin from the heaviest down
+        est2, se2, sampled2, missing2 = bench.oracle_stratified(dag, g.n, k, budget_s=120)
+        assert not missing2 and 0 < sampled2 <= eligible and est2 >= 0.0 and se2 >= 0.0

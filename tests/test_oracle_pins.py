@@ -299,10 +299,14 @@ def test_per_root_and_per_edge_values_equal_brute_force(oracle_lib, seed, relabe
         assert [int(x) for x in pr] == [int(want_root[r]) for r in roots]
         assert tot == int(want_root[roots].sum())
         pe = oracle_lib.count_per_edge(off, cols, n, k)
+        # the arc-subset form on a shuffled subset of arcs (including arcs of the last rows)
+        sub = rng.permutation(int(off[-1]))[: max(1, int(off[-1]) // 2)].astype(np.uint64)
+        sub_tot, pa = oracle_lib.count_arcs(off, cols, n, k, sub, per_arc=True)
         for u in range(n):
             for e in range(int(off[u]), int(off[u + 1])):
                 assert int(pe[e]) == want_edge.pop((u, int(cols[e])), 0), (k, u, int(cols[e]))
         assert not want_edge  # every (root, second) pair is an arc of the DAG
+        assert [int(x) for x in pa] == [int(pe[e]) for e in sub] and sub_tot == int(pe[sub].sum())
 
 
 def degeneracy_brute(g):
