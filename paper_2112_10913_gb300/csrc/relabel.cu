@@ -6,7 +6,7 @@
 // (Sec. II, Sec. IV) in rank space, where every local subgraph of the counting phase is
 // upper-triangular.
 //
-// Five launches; no block waits on another, and only the scan waits on earlier tiles:
+// Six launches; no block waits on another, and only the scan waits on earlier tiles:
 //   k_rl_prologue : rowlen[r] = 0 and perm[rank[u]] = u (the vertex of each rank);
 //   k_rl_keep     : one pass over the arcs, one chunk of 512 arcs per warp and no block-wide
 //                   barrier.  Per arc u->v the keep-test rank[v] > rank[u] (the 16 rank gathers
@@ -20,9 +20,10 @@
 //                   the largest row;
 //   k_rl_fill     : rows in RANK order, one row per lane: a row of <= 32 entries is sorted by its
 //                   lane in registers (a bitonic network of 4..32 values); longer rows are listed;
-//   k_rl_fill_mid : one listed row per warp, claimed dynamically: rows of 33..1024 entries are
-//                   sorted by the whole warp in registers (bitonic over the lanes); longer rows
-//                   are listed again for k_rl_fill_long (one block per row).
+//   k_rl_fill_mid : one listed row per warp, claimed dynamically, sorted by the whole warp in
+//                   registers (bitonic over the lanes): rows of 33..256 entries, then (second
+//                   launch, more registers per lane) 257..1024; longer rows are listed again for
+//                   k_rl_fill_long (one block per row).
 // The kernels after k_rl_keep return at once when the error word is set: offsets computed
 // after an error are not trusted.
 #include <cuda_runtime.h>
@@ -329,21 +330,27 @@ __device__ __forceinline__ void warp_sort_row(const uint32_t *src, uint32_t len,
     }
 }
 
-// Sorts a row of up to 1024 values with one warp; false when it is longer (left to the long path).
-__device__ __forceinline__ bool warp_sort_any(const uint32_t *src, uint32_t len, uint32_t *dst, int lane)
+// Sorts a row of up to MAXLEN (256 or 1024) values with one warp; false when it is longer (left
+// to the next path).
+template <uint32_t MAXLEN>
+__device__ __forceinline__ bool warp_sort_upto(const uint32_t *src, uint32_t len, uint32_t *dst, int lane)
 {
-    if (len <= 32) warp_sort_row<1>(src, len, dst, lane);
-    else if (len <= 64) warp_sort_row<2>(src, len, dst, lane);
-    else if (len <= 128) warp_sort_row<4>(src, len, dst, lane);
-    else if (len <= 256) warp_sort_row<8>(src, len, dst, lane);
-    else if (len <= 512) warp_sort_row<16>(src, len, dst, lane);
-    else if (len <= 1024) warp_sort_row<32>(src, len, dst, lane);
-    else return false;
-    return true;
+    if (len <= 32) { warp_sort_row<1>(src, len, dst, lane); return true; }
+    if (len <= 64) { warp_sort_row<2>(src, len, dst, lane); return true; }
+    if (len <= 128) { warp_sort_row<4>(src, len, dst, lane); return true; }
+    if (len <= 256) { warp_sort_row<8>(src, len, dst, lane); return true; }
+    if constexpr (MAXLEN >= 512) {
+        if (len <= 512) { warp_sort_row<16>(src, len, dst, lane); return true; }
+    }
+    if constexpr (MAXLEN >= 1024) {
+        if (len <= 1024) { warp_sort_row<32>(src, len, dst, lane); return true; }
+    }
+    return false;
 }
 
 constexpr int kFiWarps = 8;
 constexpr int kFmWarps = 4;
+constexpr int kFmMidBlocks = 8;  // blocks of kFmWarps warps per SM for rows of 33..256 entries
 constexpr uint32_t kLongCap = 32768;  // longest relabelled row this build sorts (power of 2)
 
 // Ascending bitonic sorting network over N registers (N a power of two): every index is known at
@@ -432,28 +439,31 @@ __global__ __launch_bounds__(kFiWarps * 32) void k_rl_fill(
     }
 }
 
-// Rows of 33..1024 entries, one per warp, in the order the warps claim them (one atomic per row;
-// a row's sort costs far more).  Rows above 1024 entries are listed for k_rl_fill_long.
-__global__ __launch_bounds__(kFmWarps * 32, 4) void k_rl_fill_mid(
+// Listed rows, one per warp, in the order the warps claim them (one atomic per row; a row's sort
+// costs far more).  Two instances: rows of 33..256 entries (8 registers of values per lane, so
+// that 32 warps fit an SM), then rows of 257..1024 (32 per lane, 128 registers); each lists the
+// rows it cannot take for the next (k_rl_fill_long above 1024).
+template <uint32_t MAXLEN, int MINB>
+__global__ __launch_bounds__(kFmWarps * 32, MINB) void k_rl_fill_mid(
     const uint32_t *__restrict__ perm, const uint32_t *__restrict__ kept,
     const uint64_t *__restrict__ off, const uint64_t *__restrict__ dag_off,
-    uint32_t *__restrict__ dag_cols, const uint32_t *mid_rows, const uint32_t *n_mid, uint32_t *cursor,
-    uint32_t *long_rows, uint32_t *n_long, uint32_t *err)
+    uint32_t *__restrict__ dag_cols, const uint32_t *in_rows, const uint32_t *n_in, uint32_t *cursor,
+    uint32_t *out_rows, uint32_t *n_out, uint32_t *err)
 {
     const int lane = threadIdx.x & 31;
     if (*(volatile uint32_t *)err) return;
-    const uint32_t total = *n_mid;
+    const uint32_t total = *n_in;
     for (;;) {
         uint32_t it = 0;
         if (lane == 0) it = atomicAdd(cursor, 1u);
         it = __shfl_sync(kFull, it, 0);
         if (it >= total) break;
-        const uint32_t r = mid_rows[it];
+        const uint32_t r = in_rows[it];
         // listed by k_rl_fill after its bounds checks: r < n, perm[r] < n, the row fits
         const uint64_t src = off[perm[r]], dst = dag_off[r];
         const uint32_t len = (uint32_t)(dag_off[r + 1] - dst);
-        if (!warp_sort_any(kept + src, len, dag_cols + dst, lane) && lane == 0)
-            long_rows[atomicAdd(n_long, 1u)] = r;
+        if (!warp_sort_upto<MAXLEN>(kept + src, len, dag_cols + dst, lane) && lane == 0)
+            out_rows[atomicAdd(n_out, 1u)] = r;
     }
 }
 
@@ -520,6 +530,7 @@ size_t relabel_ws_bytes(uint32_t n, uint64_t arcs)
     s.take<uint32_t>((size_t)n + 1);                        // perm
     s.take<unsigned long long>((size_t)n / kScTile + 2);    // look-back status (scan)
     s.take<uint32_t>((size_t)n + 1);                        // rows above 32 entries
+    s.take<uint32_t>((size_t)n + 1);                        // rows above 256 entries
     s.take<uint32_t>((size_t)n + 1);                        // rows above 1024 entries
     s.take<uint32_t>(arcs + 1);                             // kept ranks, in-row layout
     return s.used;
@@ -542,6 +553,7 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
     const uint32_t sc_tiles = (n + kScTile - 1) / kScTile;
     unsigned long long *sc_status = c.take<unsigned long long>((size_t)n / kScTile + 2);
     uint32_t *mid_rows = c.take<uint32_t>((size_t)n + 1);
+    uint32_t *big_rows = c.take<uint32_t>((size_t)n + 1);
     uint32_t *long_rows = c.take<uint32_t>((size_t)n + 1);
     uint32_t *kept = c.take<uint32_t>(arcs + 1);
     if (!c.ok) return cudaErrorMemoryAllocation;
@@ -553,7 +565,8 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
         return e;
     const uint32_t ntiles = (uint32_t)ntiles64;
     const int vec4 = ((uintptr_t)cols % 16) == 0;
-    uint32_t *ticket = ctr, *max_len = ctr + 2, *n_long = ctr + 3, *n_mid = ctr + 4, *cursor = ctr + 5;
+    uint32_t *ticket = ctr, *max_len = ctr + 2, *n_long = ctr + 3, *n_mid = ctr + 4, *cursor = ctr + 5,
+             *n_big = ctr + 6, *cursor_big = ctr + 7;
     if ((e = launch_tile_rows(n, arcs, off, kWkArcs, ntiles, first_row, st))) return e;
     k_rl_prologue<<<(n + 255) / 256, 256, 0, st>>>(n, rank, rowlen, perm, err);
     k_rl_keep<<<(ntiles + kWkWarps - 1) / kWkWarps, kWkWarps * 32, 0, st>>>(n, arcs, off, cols, rank, first_row,
@@ -564,14 +577,16 @@ cudaError_t launch_relabel_dag(uint32_t n, uint64_t arcs, const uint64_t *off, c
     if (grid > (uint32_t)num_sms * 8) grid = (uint32_t)num_sms * 8;
     k_rl_fill<<<grid, kFiWarps * 32, 0, st>>>(n, arcs, off, perm, kept, dag_off, dag_cols, arcs / 2,
                                               mid_rows, n_mid, err);
-    k_rl_fill_mid<<<(uint32_t)num_sms * 4, kFmWarps * 32, 0, st>>>(perm, kept, off, dag_off, dag_cols, mid_rows,
-                                                                   n_mid, cursor, long_rows, n_long, err);
+    k_rl_fill_mid<256, kFmMidBlocks><<<(uint32_t)num_sms * kFmMidBlocks, kFmWarps * 32, 0, st>>>(
+        perm, kept, off, dag_off, dag_cols, mid_rows, n_mid, cursor, big_rows, n_big, err);
+    k_rl_fill_mid<1024, 4><<<(uint32_t)num_sms * 4, kFmWarps * 32, 0, st>>>(
+        perm, kept, off, dag_off, dag_cols, big_rows, n_big, cursor_big, long_rows, n_long, err);
     const uint32_t cap_bytes = kLongCap * sizeof(uint32_t);
     if ((e = cudaFuncSetAttribute(k_rl_fill_long, cudaFuncAttributeMaxDynamicSharedMemorySize, cap_bytes)))
         return e;
     k_rl_fill_long<<<(uint32_t)num_sms, 1024, cap_bytes, st>>>(n, arcs, off, perm, kept, dag_off, dag_cols,
                                                                arcs / 2, long_rows, n_long, kLongCap, err);
-    note_launches(6);
+    note_launches(7);
     if (d_max_outdeg)
         if ((e = cudaMemcpyAsync(d_max_outdeg, max_len, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)))
             return e;
