@@ -68,6 +68,8 @@ def parse(argv=None):
                         + ",".join(EXTRAS) + ", or all / none")
     p.add_argument("--k8-budget-s", type=float, default=30.0, help="time budget of the k = 8 count")
     p.add_argument("--chunglu-ks", default="5,6")
+    p.add_argument("--chunglu-budget-s", type=float, default=0.0,
+                   help="device-time budget of each Chung-Lu count (0: none)")
     p.add_argument("--retune", action="store_true", help="batch: time every plan instead of the cache")
     return p.parse_args(argv)
 
@@ -539,7 +541,8 @@ def run_ours(args, ks):
     del flush, ws, dag_off, dag_cols, rank_t, off, cols
     torch.cuda.empty_cache()
     if "chunglu" in extras:
-        line["chunglu"] = chunglu_obj(cg, [int(k) for k in args.chunglu_ks.split(",") if k])
+        line["chunglu"] = chunglu_obj(cg, [int(k) for k in args.chunglu_ks.split(",") if k],
+                                      args.chunglu_budget_s)
         torch.cuda.empty_cache()
     if "batch" in extras:
         line["batch"] = batch_obj(args, cg)
@@ -553,9 +556,11 @@ def run_ours(args, ks):
     return line
 
 
-def chunglu_obj(cg, ks):
+def chunglu_obj(cg, ks, budget_s: float = 0.0):
     """The 4M-vertex Chung-Lu graph (exponent 2.1, average degree 30, degrees capped at 20,000,
-    50 planted cliques of 20-40 vertices): order + relabelled DAG + count per k, CUDA events."""
+    50 planted cliques of 20-40 vertices): order + relabelled DAG + count per k, CUDA events.
+    budget_s > 0 bounds each count's device time (a k that runs out is recorded without a
+    count)."""
     import torch
 
     from paper_2112_10913_gb300 import graphgen as gg
@@ -573,19 +578,29 @@ def chunglu_obj(cg, ks):
     per_k = {}
     for k in ks:
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
         a.record()
-        c, o = cg.citron_count_ex(g.n, G.dag_off, G.dag_cols, k, G.ws, G.max_outdeg, time_kernels=True,
-                                  balance=True)
+        try:
+            c, o = cg.citron_count_ex(g.n, G.dag_off, G.dag_cols, k, G.ws, G.max_outdeg, time_kernels=True,
+                                      balance=True, budget_ms=int(budget_s * 1000))
+        except cg.CitronError as exc:
+            if exc.name != "CITRON_E_BUDGET":
+                raise
+            per_k[str(k)] = {"count": None, "did_not_finish_within_s": budget_s,
+                             "stopped_after_s": time.perf_counter() - t0}
+            continue
         b.record()
         b.synchronize()
         ms = a.elapsed_time(b)
         per_k[str(k)] = dict(count=c, count_ms=ms, order_ms=t_order, edges_per_s=g.m / ((ms + t_order) / 1e3),
                              bitmap_kernel_ms=o.kernel_ms[1],
                              bitmap_kernel_tail_frac=o.busy_ms[1] / o.busy_ms[0] if o.busy_ms[0] else None)
-    tot = sum(per_k[str(k)]["count_ms"] + t_order for k in ks)
+    tot = sum(per_k[str(k)]["count_ms"] + t_order for k in ks if per_k[str(k)]["count"] is not None)
     return {"workload": "chunglu-4M beta=2.1 avg30 cap20000 + 50 planted cliques (seed 3)",
             "n": g.n, "m_undirected": g.m, "max_outdeg": G.max_outdeg, "ks": ks,
-            "edges_per_s": g.m * len(ks) / (tot / 1e3), "order_dag_ms": t_order, "per_k": per_k,
+            "edges_per_s": (g.m * sum(per_k[str(k)]["count"] is not None for k in ks) / (tot / 1e3)
+                            if tot > 0 else None),
+            "order_dag_ms": t_order, "per_k": per_k,
             "generation_s": t_gen}
 
 

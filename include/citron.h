@@ -213,6 +213,16 @@ typedef struct {
     uint32_t budget_ms;      /* in: device time the count may take (0: no limit); when it runs
                                 out, the blocks stop taking work and the call returns
                                 CITRON_E_BUDGET */
+    uint64_t *d_per_arc;     /* in: optional device array of one uint64 per DAG arc (dag_off[n]
+                                entries; k >= 3, else CITRON_E_INVALID).  When not NULL it
+                                receives, for every arc e = (u, v), the number of k-cliques whose
+                                first two vertices in the DAG order are u then v (a clique is
+                                counted once, at its first vertex, Sec. II; inside that root by
+                                its second): the count of the edge task (u, v), for localising
+                                a difference inside a root.  A debug mode: it runs the
+                                instrumented bitmap-path kernel (as CITRON_COUNT_WORK does, and
+                                fills work_ops), and the edge tasks of small and sorted-list
+                                roots one at a time. */
 } citron_count_opts;
 
 citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,

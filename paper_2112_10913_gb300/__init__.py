@@ -73,6 +73,7 @@ class CountOpts(ctypes.Structure):
         ("split_min", ctypes.c_uint32),
         ("busy_ms", ctypes.c_float * 2),
         ("budget_ms", ctypes.c_uint32),
+        ("d_per_arc", ctypes.c_void_p),
     ]
 
 
@@ -254,14 +255,17 @@ def citron_count_ex(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, 
                     stream=None, small_max: int = 0, bitmap_max: int = 0, warps_per_cta: int = 0,
                     time_kernels: bool = False, count_work: bool = False, compact_max: int = 0,
                     max_blocks: int = 0, split_min: int = 0, balance: bool = False,
-                    budget_ms: int = 0):
-    """Returns (count, CountOpts) -- the options carry work_ops, kernel_ms and busy_ms on return."""
+                    budget_ms: int = 0, per_arc=None):
+    """Returns (count, CountOpts) -- the options carry work_ops, kernel_ms and busy_ms on return.
+    per_arc: optional device uint64 array of one entry per DAG arc (k >= 3), filled with each
+    edge task's count (debug mode)."""
     o = CountOpts(small_max, bitmap_max, warps_per_cta,
                   (COUNT_TIME_KERNELS if time_kernels else 0) | (COUNT_WORK if count_work else 0)
                   | (COUNT_BALANCE if balance else 0),
                   compact_max, max_blocks, _dptr(per_root).value, 0)
     o.split_min = split_min
     o.budget_ms = budget_ms
+    o.d_per_arc = _dptr(per_arc).value
     out = ctypes.c_uint64(0)
     _check(lib().citron_count_ex(n, _dptr(dag_off), _dptr(dag_cols), k, max_outdeg, ctypes.byref(o),
                                  ctypes.byref(out), _dptr(ws), _nbytes(ws), _stream(stream)),
@@ -410,6 +414,17 @@ class DeviceGraph:
                                    per_root, stream, **tuned)[0]
         return citron_count(self.n, self.dag_off, self.dag_cols, k, self.ws, self.max_outdeg,
                             per_root, stream)
+
+    def count_per_arc(self, k: int, stream=None, **tuned) -> tuple[int, np.ndarray]:
+        """(K_k, per-arc counts): for every DAG arc e = (u, v), the k-cliques whose first two
+        vertices in the DAG order are u, v (k >= 3; a debug mode of citron_count_ex)."""
+        import torch
+
+        arcs = int(self.dag_off[-1].item())
+        pa = torch.empty(max(1, arcs), dtype=torch.int64, device=self.dag_off.device)
+        c, _ = citron_count_ex(self.n, self.dag_off, self.dag_cols, k, self.ws, self.max_outdeg,
+                               stream=stream, per_arc=pa, **tuned)
+        return c, pa[:arcs].cpu().numpy().view(np.uint64)
 
     def list(self, k: int, input_ids: bool = True, stream=None) -> np.ndarray:
         """Every k-clique as a row of k vertex ids (input ids by default), shape (K_k, k)."""

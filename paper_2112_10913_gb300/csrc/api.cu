@@ -284,6 +284,8 @@ citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint3
     CountRun run;
     if (!plan_from_opts(opts, run.plan)) return CITRON_E_INVALID;
     run.sink.per_root = (unsigned long long *)opts->d_per_root;
+    run.sink.per_arc = (unsigned long long *)opts->d_per_arc;
+    if (run.sink.per_arc && k < 3) return CITRON_E_INVALID;
     run.time_kernels = (opts->flags & CITRON_COUNT_TIME_KERNELS) != 0;
     run.count_work = (opts->flags & CITRON_COUNT_WORK) != 0;
     run.balance = (opts->flags & CITRON_COUNT_BALANCE) != 0;

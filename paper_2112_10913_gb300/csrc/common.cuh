@@ -207,6 +207,9 @@ struct RootSink {
     const uint32_t *group_of_row;        // group of each root (optional, with group_counts)
     unsigned long long *group_counts;    // per-group totals
     uint32_t ngroups;
+    // per DAG arc e = (u, v) (optional, k >= 3): the k-cliques whose first two vertices are u, v,
+    // i.e. the count of the edge task of e (zeroed by the classification pass, then added to)
+    unsigned long long *per_arc;
 
     __device__ __forceinline__ void put(uint32_t u, unsigned long long r, uint32_t *err) const
     {
@@ -283,7 +286,7 @@ struct CountPlan {
 // Options and outputs of one counting call.
 struct CountRun {
     CountPlan plan;
-    citron::RootSink sink = {nullptr, nullptr, nullptr, 0};  // per-root / per-group outputs
+    citron::RootSink sink = {nullptr, nullptr, nullptr, 0, nullptr};  // per-root / group / arc outputs
     citron::RootFilter filter;                               // roots of this pass
     bool count_work = false;                 // instrumented launch: count word operations
     bool time_kernels = false;               // record device time of the counting kernels

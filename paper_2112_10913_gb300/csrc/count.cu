@@ -33,7 +33,8 @@ namespace citron {
 __global__ void k_classify(uint32_t n, const uint64_t *__restrict__ dag_off, uint32_t need,
                            uint32_t small_max, uint32_t bitmap_max, uint32_t *small_list,
                            uint32_t *big_list, uint32_t *mid_hist, CountStats *st,
-                           unsigned long long *per_root, RootFilter filter)
+                           unsigned long long *per_root, unsigned long long *per_arc,
+                           RootFilter filter)
 {
     __shared__ uint32_t s_cnt[2], s_base[2], s_max[3];
     const int lane = threadIdx.x & 31;
@@ -47,6 +48,8 @@ __global__ void k_classify(uint32_t n, const uint64_t *__restrict__ dag_off, uin
         const uint64_t d64 = dag_off[u + 1] - dag_off[u];
         D = (uint32_t)min(d64, (uint64_t)0xffffffffull);
         if (per_root) per_root[u] = 0;
+        if (per_arc)  // debug output: every arc of the row starts at zero
+            for (uint64_t e = dag_off[u]; e < dag_off[u + 1]; e++) per_arc[e] = 0;
         if (D >= need && filter.takes(u)) cls = D <= small_max ? 0 : (D <= bitmap_max ? 2 : 1);
     }
     uint32_t off_in_warp[2] = {0, 0}, warp_base[2] = {0, 0};
@@ -260,7 +263,7 @@ cudaError_t run_count(uint32_t n, const uint64_t *dag_off, const uint32_t *dag_c
     if (n) {
         k_classify<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max,
                                           small_list, big_list, hist, st, run.sink.per_root,
-                                          run.filter);
+                                          run.sink.per_arc, run.filter);
         k_mid_bins<<<1, 1024, 0, s>>>(hist, plan.bitmap_max + 1, cursor, st);
         k_mid_scatter<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max,
                                              cursor, mid_list, run.filter);
@@ -335,7 +338,7 @@ cudaError_t run_count_async(uint32_t n, const uint64_t *dag_off, const uint32_t 
     const uint32_t need = k - 1;
     const uint32_t blocks = (n + 255) / 256;
     k_classify<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max, small_list,
-                                      big_list, hist, st, nullptr, run.filter);
+                                      big_list, hist, st, nullptr, nullptr, run.filter);
     k_mid_bins<<<1, 1024, 0, s>>>(hist, plan.bitmap_max + 1, cursor, st);
     k_mid_scatter<<<blocks, 256, 0, s>>>(n, dag_off, need, plan.small_max, plan.bitmap_max, cursor,
                                          mid_list, run.filter);

@@ -103,7 +103,20 @@ __global__ __launch_bounds__(kSmallWarps * 32) void k_count_small(
         }
         unsigned long long acc = 0;
         const uint32_t all = D == 32 ? kFull : ((1u << D) - 1);
-        small_dfs<K - 1>(all, myrow, lane, acc);
+        if (sink.per_arc) {
+            // debug output: the root's edge tasks one at a time, each (K-2)-clique count of
+            // N+(u) ∩ N+(a) stored for its arc
+            for (uint32_t a = 0; a < D; a++) {
+                const uint32_t c2 = all & __shfl_sync(kFull, myrow, a);
+                unsigned long long t = 0;
+                if (__popc(c2) >= K - 2) small_dfs<K - 2>(c2, myrow, lane, t);
+                const unsigned long long tt = warp_sum_u64(t, err);
+                if (lane == 0) sink.per_arc[base + a] = tt;
+                acc += t;
+            }
+        } else {
+            small_dfs<K - 1>(all, myrow, lane, acc);
+        }
         if (sink.wants_root_total()) {
             const unsigned long long r = warp_sum_u64(acc, err);
             if (lane == 0) sink.put(u, r, err);
@@ -971,7 +984,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     uint32_t *sL = smem;
     uint32_t *rows = smem + dcap;
     __shared__ uint32_t s_idx, s_task, s_tri, s_slot, s_u, s_units;
-    __shared__ unsigned long long s_acc[32];
+    __shared__ unsigned long long s_acc[32], s_arc[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t wsw = warp_scratch_words(dcap, compact_max);
     uint32_t *wscr = rows + (size_t)dcap * rs_cap + (size_t)w * wsw;
@@ -988,6 +1001,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
     x.compact3_max = compact_max ? 192u : 0u;
     x.pair_cap = dcap;
     const uint32_t nlist = st->n_mid;
+    if (WORK && lane == 0) s_arc[w] = 0;
     if (block_ns && threadIdx.x == 0) block_ns[2 * blockIdx.x] = global_ns();
     unsigned long long block_total = 0;  // meaningful in thread 0
     bool queue_empty = false;
@@ -1048,6 +1062,7 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
                         if (sL[j] == y) {
                             if (K == 3) {
                                 acc += 1;
+                                if (WORK && sink.per_arc) atomicAdd(&sink.per_arc[base + i], 1ull);
                             } else {
                                 atomicOr(&rows[i * RS + (j >> 5)], 1u << (j & 31));
                                 tri &= j > i;
@@ -1153,6 +1168,17 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
                     const uint32_t cnt = __reduce_add_sync(kFull, __popc(c2));
                     if (cnt >= K - 3) warp_dfs<K - 3, WORK>(x, c2, lane, acc, work);
                 }
+                if (WORK && sink.per_arc) {
+                    // debug output (instrumented kernel only): acc holds this unit's part of edge
+                    // task t alone (it restarts from zero after every unit; the warp's running
+                    // sum is kept in s_arc)
+                    const unsigned long long d = warp_sum_u64(acc, err);
+                    if (lane == 0) {
+                        if (d) atomicAdd(&sink.per_arc[base + t], d);
+                        s_arc[w] += d;
+                    }
+                    acc = 0;
+                }
             }
         }
         if (WORK) {
@@ -1160,7 +1186,13 @@ __global__ __launch_bounds__(kMidMaxWarps * 32, 1) void k_count_mid(
             if (lane == 0 && wsum) atomicAdd(work_out, wsum);
         }
         const unsigned long long ws = warp_sum_u64(acc, err);
-        if (lane == 0) s_acc[w] = ws;
+        if (lane == 0) {
+            s_acc[w] = ws;
+            if (WORK) {  // the per-arc mode's running sum (zero without it)
+                s_acc[w] += s_arc[w];
+                s_arc[w] = 0;
+            }
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long r = 0;
@@ -1259,7 +1291,42 @@ __global__ __launch_bounds__(kListWarps * 32) void k_count_list(
             continue;
         }
         unsigned long long acc = 0;
-        list_dfs<K - 1>(dag_off, dag_cols, dag_cols + base, D, buf, stride, lane, acc);
+        if (sink.per_arc) {
+            // debug output: the root's edge tasks one at a time (list_dfs's first level, with
+            // the intersection N+(u) ∩ N+(a) always listed in buf)
+            const uint32_t *C = dag_cols + base;
+            for (uint32_t i = 0; i < D; i++) {
+                const uint32_t a = C[i];
+                const uint64_t ab = dag_off[a], ae = dag_off[a + 1];
+                uint32_t out = 0;
+                for (uint32_t p = 0; p < D; p += 32) {
+                    bool hit = false;
+                    uint32_t y = 0;
+                    if (p + lane < D) {
+                        y = C[p + lane];
+                        uint64_t lo = ab, hi = ae;
+                        while (lo < hi) {
+                            const uint64_t mid = lo + (hi - lo) / 2;
+                            if (dag_cols[mid] < y) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        hit = lo < ae && dag_cols[lo] == y;
+                    }
+                    const uint32_t bal = __ballot_sync(kFull, hit);
+                    if (hit) buf[out + __popc(bal & lanemask_lt())] = y;
+                    out += __popc(bal);
+                }
+                __syncwarp();
+                unsigned long long t = 0;
+                list_dfs<K - 2>(dag_off, dag_cols, buf, out, buf + stride, stride, lane, t);
+                __syncwarp();
+                const unsigned long long tt = warp_sum_u64(t, err);
+                if (lane == 0) sink.per_arc[base + i] = tt;
+                acc += t;
+            }
+        } else {
+            list_dfs<K - 1>(dag_off, dag_cols, dag_cols + base, D, buf, stride, lane, acc);
+        }
         if (sink.wants_root_total()) {
             const unsigned long long r = warp_sum_u64(acc, err);
             if (lane == 0) sink.put(u, r, err);
@@ -1374,7 +1441,9 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         Timer t(run.time_kernels, s);
         unsigned long long *block_ns = run.balance ? aux.block_ns : nullptr;
         uint32_t grid = 0;
-        if (run.count_work)
+        // the instrumented kernel also serves the per-arc debug output (its code is compiled out
+        // of the plain kernel)
+        if (run.count_work || run.sink.per_arc)
             e = launch_mid<K, true>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, plan.split_min,
                                     aux.help, warps, smem_for(warps), dag_off, dag_cols, mid_list, st,
                                     next + 0, result, run.sink, work, block_ns, aux.budget, &grid, err, s,

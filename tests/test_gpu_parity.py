@@ -134,6 +134,24 @@ def test_per_root_counts(gpu, oracle_lib, graphs, path):
         assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
 
 
+@pytest.mark.parametrize("path", list(PATHS))
+def test_per_arc_counts(gpu, oracle_lib, graphs, path):
+    """The debug per-arc output equals the oracle's per-edge counts arc by arc on every counting
+    path (the count of each edge task: k-cliques whose first two vertices are the arc's ends),
+    and sums to the total; k < 3 is refused."""
+    for name in ("K33", "er2000+K12", "rmat-n6000"):
+        g = graphs[name]
+        G = gpu.DeviceGraph(g)
+        off, cols = G.dag_numpy()
+        for k in (3, 4, 5, 6):
+            c, pa = G.count_per_arc(k, **PATHS[path])
+            want = oracle_lib.count_per_edge(off, cols, g.n, k)
+            assert np.array_equal(pa, want), (name, k, path)
+            assert c == int(want.sum()) == G.count(k), (name, k, path)
+    with pytest.raises(gpu.CitronError):
+        gpu.DeviceGraph(graphs["fig1"]).count_per_arc(2)
+
+
 def test_closed_forms(gpu):
     # (n, k) pairs whose enumeration stays small: C(n, k-1) leaf sets at most ~1e9
     for n in (1, 2, 5, 32, 33, 64, 200):
