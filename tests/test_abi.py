@@ -117,3 +117,49 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stderr
     assert out.stdout.startswith("ok ")
+
+
+def test_python_mirrors_match_the_c_layout(tmp_path):
+    """The binding's ctypes mirrors of citron_count_opts and citron_faults have the C header's
+    field offsets and size (compiled with the host C compiler; no GPU)."""
+    import shutil
+    import subprocess
+
+    import paper_2112_10913_gb300 as cg
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"citron_count_opts": cg.CountOpts, "citron_faults": cg.Faults}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "citron.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", f"-I{ROOT / 'include'}", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            parts = line.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_per_arc_needs_k_of_three(built):
+    import paper_2112_10913_gb300 as cg
+
+    L = cg.lib()
+    out = ctypes.c_uint64(0)
+    null = ctypes.c_void_p(0)
+    o = cg.CountOpts(0, 0, 0, 0, 0, 0, None, 0)
+    o.d_per_arc = 1  # any non-NULL pointer: the check comes before any device access
+    assert L.citron_count_ex(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 2, 0, ctypes.byref(o),
+                             ctypes.byref(out), null, 0, null) == 1
