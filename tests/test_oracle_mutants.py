@@ -32,6 +32,7 @@ MUTANTS = [
     ("per-root-slot", "if (p->per_root) p->per_root[t] = c;", "if (p->per_root) p->per_root[u % p->nroots] = c;"),
     ("per-edge-slot", "st = cnt(&g, levels[0], len, k - 2, levels + 1, &per_edge[e]);",
      "st = cnt(&g, levels[0], len, k - 2, levels + 1, &per_edge[dag_off[u] + dag_off[u + 1] - 1 - e]);"),
+    ("arc-row-search", "if (dag_off[mid] <= e) lo = mid;", "if (dag_off[mid] < e) lo = mid;"),
     ("prefix-sum", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u];", "for (uint32_t u = 0; u < n; u++) dag_off[u + 1] = dag_off[u] + count[u] - (count[u] > 2);"),
 ]
 
@@ -109,6 +110,14 @@ def pins_hold() -> bool:
             got_edge = {(u, int(cols[e])): int(pe[e]) for u in range(g.n)
                         for e in range(int(off[u]), int(off[u + 1])) if pe[e]}
             if got_edge != want_edge:
+                return False
+            # the arc-subset form on a shuffled subset of arcs (the CPU baseline's unit)
+            sub = np.random.default_rng(3).permutation(int(off[-1]))[: int(off[-1]) // 2 + 1]
+            tot, pa = oracle.count_arcs(off, cols, g.n, k, sub.astype(np.uint64), per_arc=True)
+            arc_of = {e: (u, int(cols[e])) for u in range(g.n) for e in range(int(off[u]), int(off[u + 1]))}
+            if [int(x) for x in pa] != [want_edge.get(arc_of[int(e)], 0) for e in sub]:
+                return False
+            if tot != sum(want_edge.get(arc_of[int(e)], 0) for e in sub):
                 return False
         return True
     except Exception:
