@@ -165,9 +165,9 @@ def oracle_stratified(dag, n, k, budget_s, seed=2, groups=8, per=None):
     a size set by the band), timed on one thread in one worker process, round-robin over the
     bands from the heaviest down, so that every band is sampled early.  A band's time is its arc
     count times its mean time per sampled arc (inverse-probability weighting), with a standard
-    error from the spread of its groups.  Sampling stops at budget_s (the worker is stopped): a
-    band with no group done by then is left out, and the estimate is then a lower bound.
-    Returns (seconds on one thread, standard error, sampled arcs, bands left out)."""
+    error from the spread of its groups.  Sampling stops budget_s after the worker is ready (the
+    worker is stopped): a band with no group done by then is left out, and the estimate is then a
+    lower bound.  Returns (seconds on one thread, standard error, sampled arcs, bands left out)."""
     import multiprocessing as mp
     import queue as queue_mod
 
@@ -201,7 +201,9 @@ def oracle_stratified(dag, n, k, budget_s, seed=2, groups=8, per=None):
     proc = ctx.Process(target=_band_worker, args=(dag_off, dag_cols, n, k, plan, q), daemon=True)
     proc.start()
     done = {b: [] for b in sizes}
-    deadline = time.perf_counter() + budget_s
+    # the budget counts from the worker's first report: its start-up (interpreter, arrays) is not
+    # sampling time; a worker that never reports is given up after a minute
+    deadline = time.perf_counter() + 60.0
     finished, call_s = False, 0.0
     while not finished and time.perf_counter() < deadline:
         try:
@@ -212,6 +214,7 @@ def oracle_stratified(dag, n, k, budget_s, seed=2, groups=8, per=None):
             finished = True
         elif item[0] == "call":
             call_s = item[2]
+            deadline = time.perf_counter() + budget_s
         else:
             done[item[0]].append((item[1], max(0.0, item[2] - call_s)))
     if not finished:
@@ -733,13 +736,14 @@ def run_reference(args, ks):
     threads = oracle.default_threads()
     g = workload()
     budget = max(0.5, min(args.cpu_budget, 150.0 / max(1, (args.steps + args.warmup) * len(ks))))
-    times, last = [], None
+    times, last, lower = [], None, False
     for i in range(args.warmup + args.steps):
         dag, t_order = oracle_order(g)
         t = 0.0
         for k in ks:
-            t1, _, sampled, _ = oracle_stratified(dag, g.n, k, budget, seed=2 + i)
+            t1, _, sampled, missing = oracle_stratified(dag, g.n, k, budget, seed=2 + i)
             t += t_order + t1 / threads
+            lower = lower or (bool(missing) and i >= args.warmup)
         if i >= args.warmup:
             times.append(t)
         last = sampled
@@ -748,7 +752,9 @@ def run_reference(args, ks):
     sample = (f"oracle ordering + DAG on the whole graph per job; counting time per k estimated from "
               f"edge tasks (DAG arcs) stratified by their root's out-degree ({budget:.1f} s of "
               f"single-thread sampling per k, inverse-probability weighted, divided by {threads} "
-              f"threads; last k: {last} arcs)")
+              f"threads; last k: {last} arcs)"
+              + ("; some out-degree bands were not reached within the budget in a timed step: the "
+                 "time is a lower bound" if lower else ""))
     return {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
