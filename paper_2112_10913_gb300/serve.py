@@ -81,11 +81,12 @@ class ServeConfig:
 
 class DagCache:
     """Relabelled DAGs of graphs counted before, on the device: key -> (n, arcs, max_outdeg,
-    dag_off (n+1, from 0), dag_cols (ranks 0..n-1)), least recently used out first.
+    dag_off (n+1, from 0), dag_cols (ranks 0..n-1)), the oldest stored out first.
 
     The DAGs live in one device buffer allocated once (a ring: new DAGs go after the last one,
-    wrapping around to the start and pushing out the DAGs they overlap), so that caching never
-    calls the device allocator, which would synchronise the device under the other slots' work.
+    wrapping around to the start and pushing out the DAGs they overlap, i.e. the ones stored
+    longest ago), so that caching never calls the device allocator, which would synchronise the
+    device under the other slots' work.
     A DAG that a micro-batch in flight still reads is never overwritten: the new one is then not
     kept."""
 
@@ -106,7 +107,6 @@ class DagCache:
             e = self.entries.get(key)
             if e is None:
                 return None
-            self.entries.move_to_end(key)
             self.in_use[key] += 1
             return e[0]
 
