@@ -686,6 +686,18 @@ def _serve_pool(per_rate):
     return pool
 
 
+def _alone_summary(pool, alone_ms, heavy_arcs: int) -> dict:
+    """Latency of every request served alone (its floor): p50/p99 of all requests and of the
+    light ones (below the heavy lane's arc threshold), and the sum."""
+    light = [t for it, t in zip(pool, alone_ms) if not (heavy_arcs and it.graph.arcs >= heavy_arcs)]
+    out = {"p50": float(np.percentile(alone_ms, 50)), "p99": float(np.percentile(alone_ms, 99)),
+           "sum_s": float(sum(alone_ms) / 1e3)}
+    if light:
+        out["light_p50"] = float(np.percentile(light, 50))
+        out["light_p99"] = float(np.percentile(light, 99))
+    return out
+
+
 def serve_obj(cg, rates=(100, 1000), per_rate=400):
     """The request loop (continuous batching) on Poisson arrivals at the given rates: requests
     drawn from the batch distribution (seed 5) plus 2 % R-MAT scale-18 graphs; p50/p99 of all
@@ -716,9 +728,7 @@ def serve_obj(cg, rates=(100, 1000), per_rate=400):
     return {"workload": f"{per_rate} requests per rate from the batch distribution (seed 5) + 2% R-MAT "
                         "scale 18, Poisson arrivals",
             "per_rate": per, "counts_equal_alone": True,
-            "alone_latency_ms": {"p50": float(np.percentile(alone_ms, 50)),
-                                 "p99": float(np.percentile(alone_ms, 99)),
-                                 "sum_s": float(sum(alone_ms) / 1e3)},
+            "alone_latency_ms": _alone_summary(pool, alone_ms, cfg.heavy_arcs),
             "config": {k: getattr(cfg, k) for k in ("slots", "max_batch_requests", "heavy_arcs",
                                                     "heavy_sm_fraction", "hbm_budget_bytes")}}
 
@@ -829,9 +839,7 @@ def run_serve(args):
                    "slots": cfg.slots, "max_batch_requests": cfg.max_batch_requests,
                    "heavy_arcs": cfg.heavy_arcs, "heavy_sm_fraction": cfg.heavy_sm_fraction},
         "per_rate": results, "counts_equal_alone": True,
-        "alone_latency_ms": {"p50": float(np.percentile(alone_ms, 50)),
-                             "p99": float(np.percentile(alone_ms, 99)),
-                             "sum_s": float(sum(alone_ms) / 1e3)},
+        "alone_latency_ms": _alone_summary(pool, alone_ms, cfg.heavy_arcs),
     }
 
 

@@ -27,3 +27,12 @@ def test_stratified_sample_covers_the_eligible_roots(oracle_lib):
         # the default plan: every band sampled, round-robin from the heaviest down
         est2, se2, sampled2, missing2 = bench.oracle_stratified(dag, g.n, k, budget_s=120)
         assert not missing2 and 0 < sampled2 <= eligible and est2 >= 0.0 and se2 >= 0.0
+
+
+def test_alone_summary_splits_the_light_requests():
+    from types import SimpleNamespace as NS
+
+    pool = [NS(graph=NS(arcs=a)) for a in (10, 20, 5_000_000, 30)]
+    out = bench._alone_summary(pool, [1.0, 2.0, 500.0, 3.0], heavy_arcs=1 << 22)
+    assert out["light_p99"] < 3.01 and out["p99"] > 400 and abs(out["sum_s"] - 0.506) < 1e-9
+    assert "light_p99" in bench._alone_summary(pool, [1.0, 2.0, 500.0, 3.0], heavy_arcs=0)
