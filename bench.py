@@ -407,8 +407,10 @@ def run_ours(args, ks):
         counts = [r[0] for r in out]
         assert ref is None or counts == ref, "counts changed between runs"
         ref = counts
-    # instrumented (untimed) launch per k: word operations of the bitmap kernel
-    work = {k: cg.citron_count_ex(n, dag_off, dag_cols, k, ws, max_outdeg, count_work=True)[1].work_ops
+    # instrumented (untimed) launch per k: word operations of the bitmap kernel (the instrumented
+    # kernel is built for k <= 8)
+    work = {k: (cg.citron_count_ex(n, dag_off, dag_cols, k, ws, max_outdeg, count_work=True)[1].work_ops
+                if k <= 8 else None)
             for k in ks}
     # measured peak of the word operation on this device (registers only, all SMs)
     peak_ops, peak_ms = cg.citron_probe_word_ops(2, 200000)
@@ -464,10 +466,10 @@ def run_ours(args, ks):
         return None
     units = m * len(ks) * world
     value = replica_throughput(m * len(ks), world, ms_step)
-    # dominant kernel: the bitmap counting kernel of the largest k
-    kd = max(ks, key=lambda k: statistics.mean(r[3][1] for r in per_job[k]))
+    # dominant kernel: the bitmap counting kernel of the largest k with a word-op count
+    kd = max([k for k in ks if work[k] is not None] or ks, key=lambda k: statistics.mean(r[3][1] for r in per_job[k]))
     kern_ms = statistics.mean(r[3][1] for r in per_job[kd])
-    achieved = work[kd] / (kern_ms / 1e3)
+    achieved = work[kd] / (kern_ms / 1e3) if work[kd] is not None else None
     order_ms = statistics.mean(r[1] for k in ks for r in per_job[k])
     order_bytes = 8 * (n + 1) + 4 * arcs + 8 * (n + 1) + 4 * (arcs // 2) + 4 * n
     sm_mhz = clk["sm_mhz"] if clk else None
@@ -502,9 +504,9 @@ def run_ours(args, ks):
         },
         "per_k": per_k,
         "roofline": {"kernel": f"k_count_mid<{kd}> (bitmap path)", "bound": "alu",
-                     "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "achieved": achieved / 1e12 if achieved is not None else None, "peak": peak_ops / 1e12,
                      "unit": "T word-ops/s (32-bit AND+POPC)",
-                     "frac": achieved / peak_ops, "traffic": None,
+                     "frac": achieved / peak_ops if achieved is not None else None, "traffic": None,
                      "peak_source": ("measured: citron_probe_word_ops (AND+POPC+add on registers, "
                                      f"all SMs, {peak_ms:.1f} ms) before the timed steps; nominal "
                                      f"{POPC_NOMINAL_OPS / 1e12:.2f} T/s at 2070 MHz"),

@@ -184,7 +184,8 @@ citron_status citron_list(uint32_t n, const uint64_t *d_dag_off, const uint32_t 
  *   written.  Same count as citron_count.  Synchronises `stream`.
  */
 #define CITRON_COUNT_TIME_KERNELS 1u /* fill kernel_ms (events on `stream`) */
-#define CITRON_COUNT_WORK 2u         /* fill work_ops (a separately compiled, instrumented kernel) */
+#define CITRON_COUNT_WORK 2u         /* fill work_ops (a separately compiled, instrumented kernel,
+                                        built for k <= 8: larger k returns CITRON_E_UNSUPPORTED) */
 #define CITRON_COUNT_BALANCE 4u      /* fill busy_ms (each bitmap-path block's start and end) */
 typedef struct {
     uint32_t small_max;      /* in: warp-register path for out-degree <= small_max, 0..32 (0: 32) */
@@ -221,8 +222,8 @@ typedef struct {
                                 its second): the count of the edge task (u, v), for localising
                                 a difference inside a root.  A debug mode: it runs the
                                 instrumented bitmap-path kernel (as CITRON_COUNT_WORK does, and
-                                fills work_ops), and the edge tasks of small and sorted-list
-                                roots one at a time. */
+                                fills work_ops; k <= 8, else CITRON_E_UNSUPPORTED), and the edge
+                                tasks of small and sorted-list roots one at a time. */
 } citron_count_opts;
 
 citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint32_t *d_dag_cols,

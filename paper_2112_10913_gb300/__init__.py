@@ -257,8 +257,8 @@ def citron_count_ex(n: int, dag_off, dag_cols, k: int, ws, max_outdeg: int = 0, 
                     max_blocks: int = 0, split_min: int = 0, balance: bool = False,
                     budget_ms: int = 0, per_arc=None):
     """Returns (count, CountOpts) -- the options carry work_ops, kernel_ms and busy_ms on return.
-    per_arc: optional device uint64 array of one entry per DAG arc (k >= 3), filled with each
-    edge task's count (debug mode)."""
+    per_arc: optional device uint64 array of one entry per DAG arc (3 <= k <= 8), filled with
+    each edge task's count (debug mode); count_work also needs k <= 8."""
     o = CountOpts(small_max, bitmap_max, warps_per_cta,
                   (COUNT_TIME_KERNELS if time_kernels else 0) | (COUNT_WORK if count_work else 0)
                   | (COUNT_BALANCE if balance else 0),

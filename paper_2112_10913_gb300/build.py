@@ -15,8 +15,10 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 OUT_DIR = PKG / "_build"
 LIB = PKG / "libcitron.so"
-SOURCES = ["count_k11_12.cu", "count_k9_10.cu", "count_k7_8.cu", "count_k3_6.cu", "count.cu",
-           "api.cu", "order.cu", "sort.cu", "relabel.cu", "core.cu", "list.cu", "noalloc.cu", "probe.cu"]
+# longest first: the deep k compile longest and start first
+SOURCES = ["count_k12.cu", "count_k11.cu", "count_k10.cu", "count_k9.cu", "count_k8.cu", "count_k7.cu",
+           "count_k3_6.cu", "count.cu", "api.cu", "order.cu", "sort.cu", "relabel.cu", "core.cu", "list.cu",
+           "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
 

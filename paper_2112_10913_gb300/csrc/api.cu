@@ -288,6 +288,7 @@ citron_status citron_count_ex(uint32_t n, const uint64_t *d_dag_off, const uint3
     if (run.sink.per_arc && k < 3) return CITRON_E_INVALID;
     run.time_kernels = (opts->flags & CITRON_COUNT_TIME_KERNELS) != 0;
     run.count_work = (opts->flags & CITRON_COUNT_WORK) != 0;
+    if ((run.count_work || run.sink.per_arc) && k > kInstrumentedMaxK) return CITRON_E_UNSUPPORTED;
     run.balance = (opts->flags & CITRON_COUNT_BALANCE) != 0;
     run.budget_ns = (unsigned long long)opts->budget_ms * 1000000ull;
     opts->work_ops = 0;

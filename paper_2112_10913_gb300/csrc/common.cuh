@@ -273,6 +273,10 @@ struct RootFilter {
 namespace citron_host {
 
 // Path thresholds of the counting phase (see count.cu).
+// The instrumented bitmap kernel (word-op counting, per-arc output) is compiled for k <= 8 only:
+// the deep recursion of k = 9..12 takes most of the build's time, and debug modes there are rare.
+constexpr uint32_t kInstrumentedMaxK = 8;
+
 struct CountPlan {
     uint32_t small_max = 32;       // roots with out-degree <= this use the warp-register path
     uint32_t bitmap_max = 1024;    // ... <= this use the shared-memory bitmap path

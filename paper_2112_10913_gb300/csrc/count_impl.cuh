@@ -1443,12 +1443,15 @@ static cudaError_t launch_count_k(CountRun &run, const uint64_t *dag_off, const 
         uint32_t grid = 0;
         // the instrumented kernel also serves the per-arc debug output (its code is compiled out
         // of the plain kernel)
-        if (run.count_work || run.sink.per_arc)
-            e = launch_mid<K, true>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, plan.split_min,
-                                    aux.help, warps, smem_for(warps), dag_off, dag_cols, mid_list, st,
-                                    next + 0, result, run.sink, work, block_ns, aux.budget, &grid, err, s,
-                                    num_sms);
-        else
+        if (run.count_work || run.sink.per_arc) {
+            if constexpr (K <= (int)kInstrumentedMaxK)
+                e = launch_mid<K, true>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, plan.split_min,
+                                        aux.help, warps, smem_for(warps), dag_off, dag_cols, mid_list, st,
+                                        next + 0, result, run.sink, work, block_ns, aux.budget, &grid, err,
+                                        s, num_sms);
+            else
+                e = cudaErrorNotSupported;  // refused by citron_count_ex before any launch
+        } else
             e = launch_mid<K, false>(hs.n_mid, plan.max_blocks, dcap, plan.compact_max, plan.split_min,
                                      aux.help, warps, smem_for(warps), dag_off, dag_cols, mid_list, st,
                                      next + 0, result, run.sink, work, block_ns, aux.budget, &grid, err, s,

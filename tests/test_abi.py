@@ -153,7 +153,7 @@ def test_python_mirrors_match_the_c_layout(tmp_path):
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
 
 
-def test_per_arc_needs_k_of_three(built):
+def test_debug_modes_k_range(built):
     import paper_2112_10913_gb300 as cg
 
     L = cg.lib()
@@ -163,3 +163,10 @@ def test_per_arc_needs_k_of_three(built):
     o.d_per_arc = 1  # any non-NULL pointer: the check comes before any device access
     assert L.citron_count_ex(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 2, 0, ctypes.byref(o),
                              ctypes.byref(out), null, 0, null) == 1
+    # the instrumented kernel behind the debug modes is built for k <= 8
+    assert L.citron_count_ex(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 9, 0, ctypes.byref(o),
+                             ctypes.byref(out), null, 0, null) == 6
+    o.d_per_arc = None
+    o.flags = cg.COUNT_WORK
+    assert L.citron_count_ex(10, ctypes.c_void_p(1), ctypes.c_void_p(1), 12, 0, ctypes.byref(o),
+                             ctypes.byref(out), null, 0, null) == 6
